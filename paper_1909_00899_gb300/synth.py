@@ -1,0 +1,162 @@
+"""Seeded synthetic inputs for the alignment workloads.
+
+This module draws residues, lengths and substitution matrices; it holds none
+of the alignment arithmetic.  Both the oracle-side checks and the CUDA path
+consume what it returns, so it stays free of anything either side computes.
+
+Workloads (all seeded; residue codes 0..A-1, uint8):
+  protein_matrix   symmetric 20x20, diagonal U{4..11}, off-diagonal U{-4..3}
+  dna_matrix       4x4, match +1, mismatch -4
+  random_db        n sequences, lengths uniform or log-normal, iid residues
+  read_windows     DNA reads vs their own reference windows, with mutated
+                   copies and long indels (the mate-rescue stand-in)
+"""
+import numpy as np
+
+BASE_SEED = 1909_00899
+PROTEIN_A = 20
+DNA_A = 4
+
+
+def rng_for(config_index: int, salt: int = 0) -> np.random.Generator:
+    return np.random.default_rng([BASE_SEED + config_index, salt])
+
+
+def protein_matrix(rng: np.random.Generator) -> np.ndarray:
+    """Symmetric 20x20: diagonal uniform in [4, 11], off-diagonal in [-4, 3]."""
+    A = PROTEIN_A
+    M = rng.integers(-4, 4, size=(A, A))
+    M = np.triu(M, 1)
+    M = M + M.T
+    M[np.arange(A), np.arange(A)] = rng.integers(4, 12, size=A)
+    return M.astype(np.int8)
+
+
+def dna_matrix(match: int = 1, mismatch: int = -4) -> np.ndarray:
+    M = np.full((DNA_A, DNA_A), mismatch, dtype=np.int8)
+    M[np.arange(DNA_A), np.arange(DNA_A)] = match
+    return M
+
+
+def residues(rng: np.random.Generator, n: int, A: int) -> np.ndarray:
+    return rng.integers(0, A, size=int(n), dtype=np.uint8)
+
+
+def lengths_uniform(rng, n, lo, hi):
+    return rng.integers(lo, hi + 1, size=int(n)).astype(np.int64)
+
+
+def lengths_lognormal(rng, n, median, sigma, lo, hi):
+    x = rng.lognormal(mean=np.log(median), sigma=sigma, size=int(n))
+    return np.clip(np.rint(x), lo, hi).astype(np.int64)
+
+
+def lengths_loguniform(rng, n, lo, hi):
+    x = np.exp(rng.uniform(np.log(lo), np.log(hi), size=int(n)))
+    return np.clip(np.rint(x), lo, hi).astype(np.int64)
+
+
+def pack(lengths: np.ndarray, rng, A: int):
+    """Concatenated residues (uint8) and offsets (int64, n+1, offsets[0]=0)."""
+    off = np.zeros(len(lengths) + 1, dtype=np.int64)
+    np.cumsum(lengths, out=off[1:])
+    return residues(rng, int(off[-1]), A), off
+
+
+def random_db(rng, n, A, dist="uniform", **kw):
+    if dist == "uniform":
+        L = lengths_uniform(rng, n, kw["lo"], kw["hi"])
+    elif dist == "lognormal":
+        L = lengths_lognormal(rng, n, kw.get("median", 300), kw.get("sigma", 0.76),
+                              kw.get("lo", 20), kw.get("hi", 35000))
+    elif dist == "loguniform":
+        L = lengths_loguniform(rng, n, kw["lo"], kw["hi"])
+    else:
+        raise ValueError(dist)
+    return pack(L, rng, A)
+
+
+# ---------------------------------------------------------------------------
+# named workloads
+# ---------------------------------------------------------------------------
+
+def workload_protein_small(seed_salt: int = 0, n_db: int = 1000, qlen: int = 256):
+    """One protein query (256) vs 1000 db sequences, lengths U{50..500}."""
+    rng = rng_for(0, seed_salt)
+    M = protein_matrix(rng)
+    q = residues(rng, qlen, PROTEIN_A)
+    db, off = random_db(rng, n_db, PROTEIN_A, "uniform", lo=50, hi=500)
+    return dict(M=M, query=q, db=db, off=off, o=11, e=1)
+
+
+def workload_protein_scale(seed_salt: int = 0, n_db: int = 100_000,
+                           qlens=(128, 512, 2048, 5000), sigma: float = 0.76):
+    """Protein queries of the given lengths vs n_db log-normal sequences
+    (median 300, clipped to [20, 35000]); sigma 0.76 gives ~40M residues at
+    100k sequences."""
+    rng = rng_for(1, seed_salt)
+    M = protein_matrix(rng)
+    queries = [residues(rng, m, PROTEIN_A) for m in qlens]
+    db, off = random_db(rng, n_db, PROTEIN_A, "lognormal", median=300,
+                        sigma=sigma, lo=20, hi=35000)
+    return dict(M=M, queries=queries, db=db, off=off, o=11, e=1)
+
+
+def _mutate(rng, seq, identity, A):
+    s = seq.copy()
+    hit = rng.random(len(s)) >= identity
+    # substitution to a different base
+    s[hit] = (s[hit] + rng.integers(1, A, size=int(hit.sum()))) % A
+    return s
+
+
+def workload_reads(seed_salt: int = 0, n_pairs: int = 1_000_000,
+                   read_len: int = 150, win_len: int = 2000):
+    """DNA reads vs their own reference windows (mate-rescue stand-in).
+
+    Classes: 30% copies at 95% identity, 10% with a 40-200 bp indel (half
+    deletions vs the window, half insertions of random bases into the read,
+    insertion length 40-100), 60% copies at 99% identity.  Reads have length
+    read_len except the indel class (read_len +/- the indel).
+    """
+    rng = rng_for(2, seed_salt)
+    A = DNA_A
+    windows = residues(rng, n_pairs * win_len, A).reshape(n_pairs, win_len)
+    cls = rng.random(n_pairs)
+    reads = []
+    kinds = np.empty(n_pairs, dtype=np.int8)
+    for k in range(n_pairs):
+        w = windows[k]
+        c = cls[k]
+        if c < 0.30:
+            kinds[k] = 0
+            start = int(rng.integers(0, win_len - read_len + 1))
+            reads.append(_mutate(rng, w[start:start + read_len], 0.95, A))
+        elif c < 0.40:
+            if rng.random() < 0.5:  # deletion vs the window: read spans a gap
+                kinds[k] = 1
+                dl = int(rng.integers(40, 201))
+                span = read_len + dl
+                start = int(rng.integers(0, win_len - span + 1))
+                left = int(rng.integers(25, read_len - 25 + 1))
+                piece = np.concatenate([w[start:start + left],
+                                        w[start + left + dl:start + span]])
+                reads.append(_mutate(rng, piece, 0.99, A))
+            else:  # insertion of random bases into the read
+                kinds[k] = 2
+                il = int(rng.integers(40, 101))
+                start = int(rng.integers(0, win_len - read_len + 1))
+                base = w[start:start + read_len]
+                cut = int(rng.integers(25, read_len - 25 + 1))
+                ins = residues(rng, il, A)
+                reads.append(_mutate(rng, np.concatenate([base[:cut], ins, base[cut:]]), 0.99, A))
+        else:
+            kinds[k] = 3
+            start = int(rng.integers(0, win_len - read_len + 1))
+            reads.append(_mutate(rng, w[start:start + read_len], 0.99, A))
+    qlen = np.array([len(x) for x in reads], dtype=np.int64)
+    q_off = np.zeros(n_pairs + 1, dtype=np.int64)
+    np.cumsum(qlen, out=q_off[1:])
+    r_off = np.arange(n_pairs + 1, dtype=np.int64) * win_len
+    return dict(M=dna_matrix(), q=np.concatenate(reads).astype(np.uint8), q_off=q_off,
+                r=windows.reshape(-1), r_off=r_off, kinds=kinds, o=6, e=1)

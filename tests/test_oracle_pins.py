@@ -1,0 +1,210 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the
+mathematics, not by the oracle itself.
+
+ - brute-force enumeration of every local alignment on tiny inputs, with
+   asymmetric random matrices (catches a dropped term, a wrong sign or index
+   and a transposed operand in the recurrence)
+ - hand-derived golden cases (tests/golden/hand_cases.ini)
+ - closed forms: identical sequences, one-residue query, gap open so large
+   that only ungapped diagonals remain (max-sum segment per diagonal),
+   all-mismatch, empty inputs
+ - invariants: score >= 0, symmetry for symmetric matrices, transpose rule
+   for asymmetric ones
+ - the striped CPU variants of Alg. 1 (lazy-F) and Alg. 6 (scan) equal the
+   scalar recurrence for every lane count p (the transformations of Sec. II
+   are claimed to be equivalences)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_00899_gb300 import synth
+
+from golden_cases import load as load_golden
+
+
+def _rand_case(rng, A, mmax, nmax, lo=-6, hi=6):
+    M = rng.integers(lo, hi + 1, size=(A, A)).astype(np.int8)
+    m = int(rng.integers(0, mmax + 1))
+    n = int(rng.integers(0, nmax + 1))
+    return M, rng.integers(0, A, m).astype(np.uint8), rng.integers(0, A, n).astype(np.uint8)
+
+
+@pytest.mark.parametrize("A", [2, 4, 20])
+def test_gotoh_equals_brute_force(A):
+    rng = np.random.default_rng([7, A])
+    cases = 3000 if A != 20 else 2000
+    for _ in range(cases):
+        M, q, r = _rand_case(rng, A, 6, 6)
+        o = int(rng.integers(1, 13))
+        e = int(rng.integers(0, o + 1))
+        assert oracle.gotoh(q, r, M, o, e) == oracle.brute(q, r, M, o, e), (q, r, M, o, e)
+
+
+def test_gotoh_equals_brute_force_length7():
+    rng = np.random.default_rng(77)
+    for _ in range(300):
+        A = int(rng.choice([2, 4, 20]))
+        M = rng.integers(-5, 6, size=(A, A)).astype(np.int8)
+        q = rng.integers(0, A, 7).astype(np.uint8)
+        r = rng.integers(0, A, 7).astype(np.uint8)
+        o = int(rng.integers(1, 13))
+        e = int(rng.integers(0, o + 1))
+        assert oracle.gotoh(q, r, M, o, e) == oracle.brute(q, r, M, o, e)
+
+
+def test_gotoh_config_matrices_brute_force():
+    rng = np.random.default_rng(79)
+    Mp = synth.protein_matrix(rng)
+    Md = synth.dna_matrix()
+    for _ in range(800):
+        for M, A, o, e in ((Mp, 20, 11, 1), (Md, 4, 6, 1)):
+            q = rng.integers(0, A, int(rng.integers(1, 8))).astype(np.uint8)
+            r = rng.integers(0, A, int(rng.integers(1, 8))).astype(np.uint8)
+            assert oracle.gotoh(q, r, M, o, e) == oracle.brute(q, r, M, o, e)
+
+
+@pytest.mark.parametrize("case", load_golden(), ids=lambda c: c["name"])
+def test_golden_hand_cases(case):
+    got = oracle.gotoh(case["q"], case["r"], case["M"], case["o"], case["e"])
+    assert got == case["score"], case["cite"]
+    # every lane count of both striped variants reaches the same value
+    for p in (1, 2, 3, 4, 8, 16, 32):
+        assert oracle.striped_lazyf(case["q"], case["r"], case["M"], case["o"], case["e"], p) == case["score"]
+        assert oracle.striped_scan(case["q"], case["r"], case["M"], case["o"], case["e"], p) == case["score"]
+    if len(case["q"]) <= 9 and len(case["r"]) <= 9:
+        assert oracle.brute(case["q"], case["r"], case["M"], case["o"], case["e"]) == case["score"]
+
+
+def test_identical_sequences_score_diagonal_sum():
+    """With every off-diagonal entry below every diagonal entry (the seeded
+    protein matrix: off <= 3 < 4 <= diag), M[x][y] <= (M[x][x]+M[y][y])/2, so
+    no alignment of a sequence against itself beats the full diagonal."""
+    rng = np.random.default_rng(80)
+    for k in range(20):
+        M = synth.protein_matrix(rng)
+        q = synth.residues(rng, int(rng.integers(1, 400)), 20)
+        assert oracle.gotoh(q, q, M, 11, 1) == int(M[q, q].sum())
+    Md = synth.dna_matrix()
+    read = synth.residues(rng, 150, 4)
+    assert oracle.gotoh(read, read, Md, 6, 1) == 150
+
+
+def test_one_residue_query():
+    rng = np.random.default_rng(81)
+    for _ in range(200):
+        A = int(rng.choice([4, 20]))
+        M = rng.integers(-8, 9, size=(A, A)).astype(np.int8)
+        q = rng.integers(0, A, 1).astype(np.uint8)
+        r = rng.integers(0, A, int(rng.integers(1, 50))).astype(np.uint8)
+        expect = max(0, int(M[q[0], r].max()))
+        assert oracle.gotoh(q, r, M, int(rng.integers(1, 12)), 1) == expect
+
+
+def _kadane_diagonals(q, r, M):
+    best = 0
+    m, n = len(q), len(r)
+    for d in range(-(m - 1), n):
+        run = 0
+        for i in range(m):
+            j = i + d
+            if 0 <= j < n:
+                run = max(0, run + int(M[q[i], r[j]]))
+                best = max(best, run)
+    return best
+
+
+def test_huge_gap_open_reduces_to_diagonal_max_segments():
+    rng = np.random.default_rng(82)
+    for _ in range(200):
+        A = int(rng.choice([4, 20]))
+        M = rng.integers(-6, 7, size=(A, A)).astype(np.int8)
+        q = rng.integers(0, A, int(rng.integers(1, 40))).astype(np.uint8)
+        r = rng.integers(0, A, int(rng.integers(1, 40))).astype(np.uint8)
+        assert oracle.gotoh(q, r, M, 1_000_000, 1) == _kadane_diagonals(q, r, M)
+
+
+def test_all_mismatch_is_zero_and_empty_inputs():
+    Md = synth.dna_matrix()
+    q = np.zeros(30, np.uint8)
+    r = np.full(40, 2, np.uint8)
+    assert oracle.gotoh(q, r, Md, 6, 1) == 0
+    assert oracle.gotoh(q[:0], r, Md, 6, 1) == 0
+    assert oracle.gotoh(q, r[:0], Md, 6, 1) == 0
+    assert oracle.striped_scan(q[:0], r, Md, 6, 1, 4) == 0
+    assert oracle.striped_lazyf(q, r[:0], Md, 6, 1, 4) == 0
+
+
+def test_nonnegative_symmetry_and_transpose():
+    rng = np.random.default_rng(83)
+    for _ in range(300):
+        A = int(rng.choice([4, 20]))
+        Ms = synth.protein_matrix(rng) if A == 20 else synth.dna_matrix()
+        Ma = rng.integers(-6, 7, size=(A, A)).astype(np.int8)
+        q = rng.integers(0, A, int(rng.integers(0, 60))).astype(np.uint8)
+        r = rng.integers(0, A, int(rng.integers(0, 60))).astype(np.uint8)
+        o = int(rng.integers(1, 13))
+        e = int(rng.integers(0, o + 1))
+        s = oracle.gotoh(q, r, Ms, o, e)
+        assert s >= 0
+        assert s == oracle.gotoh(r, q, Ms, o, e)
+        assert oracle.gotoh(q, r, Ma, o, e) == oracle.gotoh(r, q, np.ascontiguousarray(Ma.T), o, e)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 8, 16, 32, 64])
+def test_striped_variants_match_scalar(p):
+    """Alg. 1 and Alg. 6 on the CPU equal the definition for every p,
+    including gap-heavy inputs where carries cross many segments."""
+    rng = np.random.default_rng([84, p])
+    Mp = synth.protein_matrix(rng)
+    Md = synth.dna_matrix()
+    for t in range(60):
+        if t % 2:
+            M, A, o, e = Mp, 20, 11, 1
+        else:
+            M, A, o, e = Md, 4, 6, 1
+        if t % 5 == 0:
+            o = int(rng.integers(1, 13))
+            e = int(rng.integers(0, o + 1))
+        X = rng.integers(0, A, int(rng.integers(3, 50))).astype(np.uint8)
+        Y = rng.integers(0, A, int(rng.integers(0, 90))).astype(np.uint8)
+        Z = rng.integers(0, A, int(rng.integers(3, 50))).astype(np.uint8)
+        if t % 3 == 0:
+            q, r = np.concatenate([X, Y, Z]), np.concatenate([X, Z])
+        elif t % 3 == 1:
+            q, r = np.concatenate([X, Z]), np.concatenate([X, Y, Z])
+        else:
+            q, r = np.concatenate([X, Y]), np.concatenate([Z, Y, X])
+        want = oracle.gotoh(q, r, M, o, e)
+        assert oracle.striped_lazyf(q, r, M, o, e, p) == want
+        assert oracle.striped_scan(q, r, M, o, e, p) == want
+
+
+def test_lazyf_worst_case_needs_more_rounds():
+    """A long query-only insertion makes the lazy-F loop run many steps
+    (the corrective factor C of Sec. I grows with p)."""
+    rng = np.random.default_rng(85)
+    Md = synth.dna_matrix()
+    X = synth.residues(rng, 60, 4)
+    Y = synth.residues(rng, 150, 4)
+    Z = synth.residues(rng, 60, 4)
+    q = np.concatenate([X, Y, Z])
+    r = np.concatenate([X, Z])
+    _, steps_adv = oracle.striped_lazyf(q, r, Md, 6, 1, 16, return_steps=True)
+    qr = synth.residues(rng, len(q), 4)
+    _, steps_rand = oracle.striped_lazyf(qr, r, Md, 6, 1, 16, return_steps=True)
+    assert steps_adv > steps_rand
+
+
+def test_threaded_batch_and_pairs_equal_single_calls():
+    rng = np.random.default_rng(86)
+    M = synth.protein_matrix(rng)
+    q = synth.residues(rng, 97, 20)
+    db, off = synth.random_db(rng, 50, 20, "uniform", lo=0, hi=120)
+    out = oracle.gotoh_batch(q, db, off, M, 11, 1, nthreads=4)
+    for k in range(50):
+        assert out[k] == oracle.gotoh(q, db[off[k]:off[k + 1]], M, 11, 1)
+    qs, qoff = synth.random_db(rng, 50, 20, "uniform", lo=0, hi=80)
+    outp = oracle.gotoh_pairs(qs, qoff, db, off, M, 11, 1, nthreads=3)
+    for k in range(50):
+        assert outp[k] == oracle.gotoh(qs[qoff[k]:qoff[k + 1]], db[off[k]:off[k + 1]], M, 11, 1)
