@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark: scan-F striped Smith-Waterman/Gotoh on GB300.
+
+Workload (one step): protein queries of lengths 128, 512, 2048 and 5000
+against 100,000 database sequences with log-normal lengths (median 300,
+sigma 0.76, clipped to [20, 35000], ~40M residues), seeded 20x20 matrix,
+gap open 11, extend 1.  Every step builds the four query profiles and runs
+sw_align_batch for each query; the lazy-F kernel runs the same step for the
+comparison.  Metric: GCUPS = sum over alignments of m*n / seconds / 1e9.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Under torchrun every rank runs its own replica of
+the workload (the alignments are independent; no collective on the data
+path) and the time is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+QLENS = (128, 512, 2048, 5000)
+METRIC = "GCUPS scan-F (bit-exact) vs lazy-F"
+WORKLOAD = ("protein queries m in {128,512,2048,5000} vs 100k db seqs, log-normal lengths "
+            "(median 300, sigma 0.76, clip [20,35000]), o=11 e=1")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lane", default="auto", choices=["auto", "i32", "i16x2", "i8x4"])
+    ap.add_argument("--n-db", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lazyf", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU work of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline_oracle(w, qlens, target_s):
+    """The oracle (scalar int32 Gotoh, all host cores) on a bounded sample of
+    the same workload: every query against every k-th database sequence."""
+    import numpy as np
+
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    off = w["off"]
+    n = len(off) - 1
+    lens = np.diff(off)
+    # calibrate on a small slice, then size the sample for ~target_s seconds
+    probe_ids = np.arange(0, n, max(1, n // 200))
+    t0 = time.perf_counter()
+    cells = 0
+    for q in w["queries"]:
+        sub_db, sub_off = _subset(w["db"], off, probe_ids)
+        oracle.gotoh_batch(q, sub_db, sub_off, w["M"], w["o"], w["e"], nthreads=cores)
+        cells += len(q) * int(lens[probe_ids].sum())
+    rate = cells / max(time.perf_counter() - t0, 1e-6)
+    full_cells = sum(qlens) * int(lens.sum())
+    frac = min(1.0, target_s * rate / full_cells)
+    step = max(1, int(round(1.0 / frac)))
+    ids = np.arange(0, n, step)
+    sub_db, sub_off = _subset(w["db"], off, ids)
+    t0 = time.perf_counter()
+    cells = 0
+    for q in w["queries"]:
+        oracle.gotoh_batch(q, sub_db, sub_off, w["M"], w["o"], w["e"], nthreads=cores)
+        cells += len(q) * int(lens[ids].sum())
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": "all %d queries vs every %d-th db sequence (%d seqs, %.3g cells, %.1f s)"
+                      % (len(w["queries"]), step, len(ids), cells, dt)}
+
+
+def _subset(db, off, ids):
+    import numpy as np
+    parts = [db[off[i]:off[i + 1]] for i in ids]
+    sub_off = np.zeros(len(ids) + 1, dtype=np.int64)
+    np.cumsum([len(p) for p in parts], out=sub_off[1:])
+    return np.concatenate(parts).astype(np.uint8), sub_off
+
+
+def run_reference(args):
+    """The reference arm: the oracle as it stands on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1909_00899_gb300 import synth
+    w = synth.workload_protein_scale(n_db=args.n_db, qlens=QLENS)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline_oracle(w, QLENS, per_step)
+        if k >= args.warmup:
+            vals.append(cb)
+    v = statistics.median([c["value"] for c in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"],
+                             "value": v, "unit": "GCUPS"},
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1909_00899_gb300 import build as libbuild
+    from paper_1909_00899_gb300 import sw, synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    libbuild.build()
+    lane = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2,
+            "i8x4": sw.SW_LANE_I8X4}[args.lane]
+
+    w = synth.workload_protein_scale(n_db=args.n_db, qlens=QLENS)
+    M, o, e = w["M"], w["o"], w["e"]
+    n_db = len(w["off"]) - 1
+    total_res = int(w["off"][-1])
+    cells_step = sum(QLENS) * total_res
+    stream = torch.cuda.current_stream()
+    db_d = torch.from_numpy(w["db"]).cuda()
+    off_d = torch.from_numpy(w["off"]).cuda()
+    outs = [torch.zeros(n_db, dtype=torch.int32, device="cuda") for _ in QLENS]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(lazy=False, timers=None):
+        profs = []
+        for i, q in enumerate(w["queries"]):
+            if timers is not None:
+                timers[i][0].record(stream)
+            p = sw.Profile(q, M, sw.SW_LANE_I32 if lazy else lane, stream=stream)
+            fn = sw.sw_align_lazyf_batch if lazy else sw.sw_align_batch
+            fn(p, db_d, off_d, o, e, outs[i], stream=stream)
+            if timers is not None:
+                timers[i][1].record(stream)
+            profs.append(p)
+        return profs
+
+    def timed(nsteps, lazy=False):
+        for _ in range(args.warmup):
+            step(lazy)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        total_ms = 0.0
+        per_query = [0.0] * len(QLENS)
+        keep = []
+        for _ in range(nsteps):
+            flush.zero_()  # L2 flush between timed steps (db is 40 MB < 129 MB L2)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in QLENS]
+            keep.append((step(lazy, ev), ev))
+        torch.cuda.synchronize()
+        for _, ev in keep:
+            for i, (a, b) in enumerate(ev):
+                t = a.elapsed_time(b)
+                per_query[i] += t
+                total_ms += t
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, per_query
+
+    # correctness spot check against the oracle on a sample (not timed)
+    check = sample_check(w, outs, step, rank)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, per_q = timed(args.steps)
+    clocks = sampler.stop()
+    gcups = cells_step * args.steps * world / (total_ms * 1e-3) / 1e9
+
+    lazy = None
+    if not args.no_lazyf:
+        lsteps = max(1, min(args.steps, 2))
+        lms, lper = timed(lsteps, lazy=True)
+        lazy = {"value": cells_step * lsteps / (lms * 1e-3) / 1e9, "unit": "GCUPS",
+                "per_query_gcups": {str(m): sum(QLENS) and m * total_res * lsteps / (t * 1e-3) / 1e9
+                                    for m, t in zip(QLENS, lper)}}
+
+    # end to end through the public API: host (pinned) inputs copied in,
+    # scores copied out, inside the timed region
+    e2e = run_e2e(w, lane, args, stream, cells_step)
+
+    # roofline of the dominant kernel (the scan-F batch kernel)
+    prof0 = sw.Profile(w["queries"][-1], M, lane)
+    plan = prof0.plan()
+    prof0.free()
+    cells_per_op = {1: 1, 2: 2, 3: 4}[plan["lane_type"]]
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = sms * 128 * mhz * 1e6 / (6.0 / cells_per_op) / 1e9
+    probe = sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
+    launches_per_step = 0
+    for m in QLENS:
+        pf = sw.Profile(np.zeros(m, np.uint8), M, lane)
+        pl = pf.plan()
+        pf.free()
+        c32 = -(-m // 512) if m > 256 else 1
+        packed = pl["lane_type"] != sw.SW_LANE_I32
+        launches_per_step += (2 if packed else 1) + 3 + pl["chunks"] + ((1 + c32) if packed else 0)
+
+    line = {
+        "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "s16x2+int32" if cells_per_op == 2 else
+        ("int32" if cells_per_op == 1 else "s8x4+int32"), "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_db": n_db, "db_residues": total_res,
+                   "cells_per_step": cells_step, "lane": args.lane, "plan_m5000": plan,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "per_query_gcups": {str(m): m * total_res * args.steps / (t * 1e-3) / 1e9 for m, t in zip(QLENS, per_q)},
+        "lazyf": lazy,
+        "scan_vs_lazyf": (gcups / world / lazy["value"]) if lazy else None,
+        "roofline": {"bound": "alu", "achieved": gcups / world, "peak": peak, "unit": "GCUPS",
+                     "frac": gcups / world / peak, "traffic": None,
+                     "peak_basis": "%d SMs x 128 int32 lane-instr/clk x %.0f MHz (median sampled) / %g instr per cell"
+                                   % (sms, mhz, 6.0 / cells_per_op),
+                     "probe_gcups": probe, "frac_of_probe": gcups / world / probe},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "check": check,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(w, QLENS, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def sample_check(w, outs, step, rank):
+    """Scores of a sample of sequences, per query, against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    profs = step()
+    torch.cuda.synchronize()
+    del profs
+    n = len(w["off"]) - 1
+    rng = np.random.default_rng(7)
+    ids = np.sort(rng.choice(n, size=min(n, 64), replace=False))
+    sub_db, sub_off = _subset(w["db"], w["off"], ids)
+    bad = 0
+    for q, out in zip(w["queries"], outs):
+        want = oracle.gotoh_batch(q, sub_db, sub_off, w["M"], w["o"], w["e"])
+        got = out.cpu().numpy()[ids]
+        bad += int((got != want).sum())
+    if bad:
+        raise SystemExit("bench: %d sampled scores differ from the oracle" % bad)
+    return {"sampled": int(len(ids)) * len(w["queries"]), "mismatches": 0}
+
+
+def run_e2e(w, lane, args, stream, cells_step):
+    import torch
+
+    from paper_1909_00899_gb300 import sw
+    db_h = torch.from_numpy(w["db"]).pin_memory()
+    off_h = torch.from_numpy(w["off"]).pin_memory()
+    n_db = len(w["off"]) - 1
+    out_h = [torch.empty(n_db, dtype=torch.int32).pin_memory() for _ in QLENS]
+    db_d = torch.empty_like(db_h, device="cuda")
+    off_d = torch.empty_like(off_h, device="cuda")
+    outs = [torch.empty(n_db, dtype=torch.int32, device="cuda") for _ in QLENS]
+
+    def one():
+        db_d.copy_(db_h, non_blocking=True)
+        off_d.copy_(off_h, non_blocking=True)
+        profs = []
+        for i, q in enumerate(w["queries"]):
+            p = sw.Profile(q, w["M"], lane, stream=stream)
+            sw.sw_align_batch(p, db_d, off_d, w["o"], w["e"], outs[i], stream=stream)
+            out_h[i].copy_(outs[i], non_blocking=True)
+            profs.append(p)
+        return profs
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    keep = [one() for _ in range(steps)]
+    b.record(stream)
+    torch.cuda.synchronize()
+    del keep
+    ms = a.elapsed_time(b)
+    h2d = db_h.numel() + off_h.numel() * 8 + sum(len(q) for q in w["queries"]) + 400 * 2 * len(QLENS)
+    d2h = 4 * n_db * len(QLENS)
+    return {"value": cells_step * steps / (ms * 1e-3) / 1e9, "unit": "GCUPS",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

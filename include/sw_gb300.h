@@ -1,0 +1,164 @@
+/*
+ * sw_gb300.h — C ABI of the GB300 (sm_103a) score-only Smith-Waterman/Gotoh
+ * library: striped query layout with the F dependency between segments
+ * resolved by a max-plus prefix scan (arXiv:1909.00899, Alg. 6), plus the
+ * lazy-F correction loop (Alg. 1) as the plain-method comparison.
+ *
+ * What is computed (Sec. I): for a query Q (length m) and each reference
+ * sequence R (length n), the optimal local alignment score with affine gaps,
+ *   E(q,r) = max(H(q,r-1) - o, E(q,r-1) - e)
+ *   F(q,r) = max(H(q-1,r) - o, F(q-1,r) - e)
+ *   H(q,r) = max(0, H(q-1,r-1) + M[Q_q][R_r], E(q,r), F(q,r))
+ *   score  = max over q,r of H(q,r)   (0 when m == 0 or n == 0)
+ * so a gap run of k residues costs o + (k-1)*e (Alg. 1 charges GapOpen for
+ * the first residue and GapExtend for each further one).  M is indexed
+ * [query residue][reference residue] (the query profile of Alg. 1 is built
+ * from the query).  Scores are exact int32 whatever lane type computes them.
+ *
+ * Conventions for every call
+ *  - Residues are codes 0..A-1 in uint8.  A database code >= A is read as
+ *    an unknown residue that never scores (its column cannot raise H
+ *    through a match); query codes >= A are rejected by sw_profile_build.
+ *  - "device" pointers are CUDA device memory on the current device, owned
+ *    by the caller; "host" pointers are host memory owned by the caller and
+ *    only read during the call.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Align
+ *    calls are asynchronous on that stream: they return after enqueueing
+ *    work; results are valid once the stream reaches that point.
+ *  - Return value: SW_OK (0) or a negative SW_ERR_* code; sw_last_error()
+ *    then returns a message (thread-local, valid until the next call on the
+ *    same thread).  Invalid arguments are rejected before any CUDA call.
+ *  - Library scratch (length-sorted work order, boundary rows of long
+ *    queries, overflow lists) comes from a library-owned stream-ordered
+ *    memory pool and is released on the call's stream.
+ */
+#ifndef SW_GB300_H
+#define SW_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SW_OK 0
+#define SW_ERR_INVALID (-1)  /* bad argument (null pointer, range, shape)  */
+#define SW_ERR_CUDA (-2)     /* a CUDA runtime call or a launch failed      */
+#define SW_ERR_NOMEM (-3)    /* device or host allocation failed            */
+#define SW_ERR_TIMEOUT (-4)  /* sw_stream_sync gave up waiting              */
+#define SW_ERR_RANGE (-5)    /* matrix/gap values do not fit the lane type  */
+
+/* lane types: how many cells one 32-bit register carries */
+#define SW_LANE_AUTO 0   /* library picks (packed lanes + exact rescore)   */
+#define SW_LANE_I32 1    /* one int32 cell per register                    */
+#define SW_LANE_I16X2 2  /* two int16 cells per register, DPX s16x2 ops    */
+#define SW_LANE_I8X4 3   /* four int8 cells per register, saturating SIMD  */
+
+typedef struct sw_profile sw_profile; /* opaque, owned by the library */
+
+/*
+ * sw_profile_build — striped query profile (Alg. 1/6 "vprofile": for each
+ * residue c, the score M[Q_q][c] of every query position q, laid out so that
+ * lane l of an alignment holds positions l*segLen .. l*segLen+segLen-1).
+ *   query         host, qlen codes in 0..alphabet-1 (may be NULL if qlen 0)
+ *   qlen          >= 0
+ *   subst_matrix  host, alphabet*alphabet int8, row-major [query][reference]
+ *   alphabet      1..32
+ *   lane_type     SW_LANE_*; the layout (lanes per alignment, segment
+ *                 length, query chunks) is chosen from qlen and lane_type
+ *   cuda_stream   stream for the upload and the profile-build kernel
+ *   out           receives the profile; free with sw_profile_free
+ * Device memory for the profile is allocated here (synchronously) on the
+ * current device.  Errors: SW_ERR_INVALID (qlen < 0, alphabet out of range,
+ * null pointers), SW_ERR_NOMEM, SW_ERR_CUDA.
+ */
+int sw_profile_build(const uint8_t *query, int32_t qlen,
+                     const int8_t *subst_matrix, int32_t alphabet,
+                     int32_t lane_type, void *cuda_stream, sw_profile **out);
+
+/* Releases a profile (waits for the device to finish with it).  NULL ok. */
+int sw_profile_free(sw_profile *prof);
+
+/* Describes a profile's plan: lanes per alignment, segment length per lane,
+ * query chunks, lane type actually used.  Any out pointer may be NULL. */
+int sw_profile_plan(const sw_profile *prof, int32_t *lanes, int32_t *seg_len,
+                    int32_t *chunks, int32_t *lane_type);
+
+/*
+ * sw_align_batch — scores of one profiled query against n_db database
+ * sequences with the scan-F method (Alg. 6): per reference column each lane
+ * runs its segment with a zero F carry, the carry between segments is the
+ * max-plus prefix scan over lanes with weight segLen*e per hop, and the
+ * correction of H (and of E) is deferred into the next column's pass.
+ *   db_residues  device, concatenated residue codes
+ *   db_offsets   device, int64[n_db + 1], offsets[0] = 0, non-decreasing;
+ *                sequence k is db_residues[offsets[k] .. offsets[k+1])
+ *   n_db         >= 0 (0 is a no-op)
+ *   gap_open     o >= 1;  gap_extend  0 <= e <= o  (the carry of Alg. 4-6
+ *                only extends gaps, exact only when e <= o)
+ *   scores_out   device, int32[n_db]
+ * Errors: SW_ERR_INVALID (null pointers, n_db < 0, gap costs out of range),
+ * SW_ERR_RANGE (values too large even for int32 accumulation),
+ * SW_ERR_NOMEM, SW_ERR_CUDA.  Offsets are not validated on the device.
+ */
+int sw_align_batch(const sw_profile *prof, const uint8_t *db_residues,
+                   const int64_t *db_offsets, int64_t n_db, int32_t gap_open,
+                   int32_t gap_extend, int32_t *scores_out, void *cuda_stream);
+
+/*
+ * sw_align_lazyf_batch — same inputs, outputs and errors as sw_align_batch,
+ * computed with the lazy-F correction loop of Alg. 1 (up to p rounds of
+ * shift-and-correct per column, leaving as soon as no lane's carried F can
+ * raise anything).  Always int32 lanes.  The comparison kernel.
+ */
+int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues,
+                         const int64_t *db_offsets, int64_t n_db,
+                         int32_t gap_open, int32_t gap_extend,
+                         int32_t *scores_out, void *cuda_stream);
+
+/*
+ * sw_align_pairs — n_pairs independent alignments, pair k aligning query
+ * q[q_off[k] .. q_off[k+1]) against reference r[r_off[k] .. r_off[k+1])
+ * with the scan-F method (read-vs-window batches; each pair's profile is
+ * built inside the kernel from its own query).
+ *   q, r            device residue codes;  q_off, r_off  device int64[n+1]
+ *   subst_matrix    host, alphabet*alphabet int8 [query][reference]
+ *                   (copied into the launch parameters)
+ *   lane_type       SW_LANE_*: packed types flag pairs whose score may have
+ *                   left the lane range and rescore them in int32
+ *   scores_out      device int32[n_pairs]
+ * Query lengths up to 4096 per pair.  Errors as sw_align_batch.
+ */
+int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r,
+                   const int64_t *r_off, int64_t n_pairs,
+                   const int8_t *subst_matrix, int32_t alphabet,
+                   int32_t gap_open, int32_t gap_extend, int32_t lane_type,
+                   int32_t *scores_out, void *cuda_stream);
+
+/* Waits for cuda_stream with a bound: SW_OK when the stream is idle,
+ * SW_ERR_TIMEOUT after timeout_ms milliseconds (the work keeps running and
+ * the context stays usable), SW_ERR_CUDA if the stream reported an error. */
+int sw_stream_sync(void *cuda_stream, int64_t timeout_ms);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *sw_last_error(void);
+
+/*
+ * sw_probe_cell_rate — measures the ALU ceiling of the cell update: every
+ * thread of a full-device grid updates independent cells with exactly the
+ * per-cell instruction sequence of the scan-F pass (no loads, no
+ * shuffles, no scan).  Writes cells per second (host double) for the lane
+ * type (SW_LANE_I32, _I16X2 or _I8X4).  Synchronises cuda_stream.  Used as
+ * the measured denominator of the integer roofline.
+ */
+int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_second,
+                       void *cuda_stream);
+
+/* Library version, e.g. "0.1.0". */
+const char *sw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SW_GB300_H */

@@ -1,0 +1,482 @@
+// C ABI of the library (declared in include/sw_gb300.h): argument checks,
+// plans, library-owned scratch, launches.  Every compute step runs in the
+// kernels of this directory; there is no host fallback.
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <string>
+#include <thread>
+
+#include "sw_gb300.h"
+#include "sw_internal.h"
+
+namespace swg {
+int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+}  // namespace swg
+
+using swg::Plan;
+
+struct sw_profile {
+    int device = 0;
+    int32_t qlen = 0, A = 0, lane = 0;
+    Plan plan;    // plan of the requested lane type
+    Plan plan32;  // int32 plan: lazy-F and the rescore of flagged alignments
+    uint8_t *d_query = nullptr;
+    int8_t *d_M = nullptr;
+    int8_t *d_prof = nullptr;
+    int8_t *d_prof32 = nullptr;
+    int32_t maxM = 0, minM = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(int err, const char *what)
+{
+    return fail(err == (int)cudaErrorMemoryAllocation ? SW_ERR_NOMEM : SW_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString((cudaError_t)err));
+}
+
+int num_sms_of(int dev)
+{
+    static std::mutex mu;
+    static int cache[64] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64)
+        return 1;
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+
+// Keep freed scratch in the device's default pool instead of returning it
+// at every synchronisation (set once per device).
+void keep_pool_warm(int dev)
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || done[dev])
+        return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+struct Choice {
+    int L, S;
+};
+
+// Lanes per alignment and segment length per lane type, smallest chunk that
+// holds the query first; longer queries use the last entry in chunks.
+const Choice kI32[] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {32, 16}};
+const Choice kI16[] = {{8, 8}, {16, 8}, {32, 8}, {32, 16}};
+const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
+
+Plan choose_plan(int32_t qlen, int lane)
+{
+    const Choice *tab = kI32;
+    int n = 5;
+    if (lane == SW_LANE_I16X2) {
+        tab = kI16;
+        n = 4;
+    } else if (lane == SW_LANE_I8X4) {
+        tab = kI8;
+        n = 3;
+    }
+    Plan p;
+    p.lane = lane;
+    int k = 0;
+    while (k + 1 < n && tab[k].L * tab[k].S < qlen)
+        ++k;
+    p.L = tab[k].L;
+    p.S = tab[k].S;
+    const int QC = p.L * p.S;
+    p.C = qlen > 0 ? (qlen + QC - 1) / QC : 0;
+    return p;
+}
+
+// Largest score bias and scan weights a lane type must hold.
+bool lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan &pl)
+{
+    if (lane == SW_LANE_I32)
+        return true;
+    const int64_t ceil = lane == SW_LANE_I16X2 ? 32767 : 127;
+    if ((int64_t)pf->maxM + o > ceil)
+        return false;
+    if (o > ceil)
+        return false;
+    if (lane == SW_LANE_I16X2) {
+        // scan hop weights and decays stay far from the wrap point
+        if ((int64_t)o + (int64_t)pl.L * pl.S * e + 256 > 16000)
+            return false;
+    }
+    return true;
+}
+
+struct Scratch {
+    void *base = nullptr;
+    cudaStream_t st = nullptr;
+    ~Scratch()
+    {
+        if (base)
+            cudaFreeAsync(base, st);
+    }
+};
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int check_align_args(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o,
+                     int32_t e, int32_t *scores)
+{
+    if (!prof)
+        return fail(SW_ERR_INVALID, "profile is NULL");
+    if (n_db < 0)
+        return fail(SW_ERR_INVALID, "n_db < 0 (%lld)", (long long)n_db);
+    if (n_db > INT32_MAX - 1024)
+        return fail(SW_ERR_INVALID, "n_db too large (%lld)", (long long)n_db);
+    if (n_db > 0 && (!db || !off || !scores))
+        return fail(SW_ERR_INVALID, "null device pointer");
+    if (o < 1)
+        return fail(SW_ERR_INVALID, "gap_open must be >= 1 (got %d)", o);
+    if (e < 0 || e > o)
+        return fail(SW_ERR_INVALID, "gap_extend must satisfy 0 <= e <= gap_open (got e=%d, o=%d)", e, o);
+    if (o > (1 << 20))
+        return fail(SW_ERR_RANGE, "gap_open too large for int32 accumulation (%d)", o);
+    if ((int64_t)prof->qlen * std::max(prof->maxM, 0) >= (1LL << 24))
+        return fail(SW_ERR_RANGE, "query length x largest score exceeds the int32 working range");
+    return SW_OK;
+}
+
+int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cudaStream_t st)
+{
+    if (pl.lane == SW_LANE_I32)
+        return swg::launch_batch_i32(pl, lazy, a, sms, st);
+    if (pl.lane == SW_LANE_I16X2)
+        return swg::launch_batch_i16(pl, a, sms, st);
+    return swg::launch_batch_i8(pl, a, sms, st);
+}
+
+int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o, int32_t e,
+               int32_t *scores, void *stream, bool lazy)
+{
+    int rc = check_align_args(prof, db, off, n_db, o, e, scores);
+    if (rc)
+        return rc;
+    if (n_db == 0)
+        return SW_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prof->qlen == 0) {
+        cudaError_t err = cudaMemsetAsync(scores, 0, sizeof(int32_t) * (size_t)n_db, st);
+        return err == cudaSuccess ? SW_OK : cuda_fail(err, "cudaMemsetAsync");
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != prof->device)
+        return fail(SW_ERR_INVALID, "profile built on device %d, current device is %d", prof->device, dev);
+    keep_pool_warm(dev);
+    const int sms = num_sms_of(dev);
+
+    int lane = lazy ? SW_LANE_I32 : prof->lane;
+    if (lane != SW_LANE_I32 && !lane_fits(lane, prof, o, e, prof->plan))
+        lane = SW_LANE_I32;  // values do not fit the packed lanes: exact int32 throughout
+    const Plan main = lane == SW_LANE_I32 ? prof->plan32 : prof->plan;
+    const int8_t *main_prof = lane == SW_LANE_I32 ? prof->d_prof32 : prof->d_prof;
+    const bool packed = lane != SW_LANE_I32;
+    const int C32 = prof->plan32.C;
+
+    // total residues, needed only to size the boundary rows of long queries
+    int64_t total = 0;
+    const bool chunked = main.C > 1 || (packed && C32 > 1);
+    if (chunked) {
+        cudaError_t err = cudaMemcpyAsync(&total, off + n_db, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess)
+            err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess)
+            return cuda_fail(err, "reading db_offsets[n_db]");
+        if (total < 0)
+            return fail(SW_ERR_INVALID, "db_offsets[n_db] < 0");
+    }
+
+    const size_t n = (size_t)n_db;
+    const int ncount = main.C + (packed ? C32 : 0) + 2;
+    const size_t sz_order = align_up(n * 4);
+    const size_t sz_zero = align_up((2 * swg::NBINS + ncount) * 4);
+    const size_t sz_list = packed ? align_up(n * 4) : 0;
+    const size_t sz_bnd = chunked ? align_up((size_t)total * sizeof(int2) + 16) : 0;
+    Scratch sc;
+    sc.st = st;
+    cudaError_t err = cudaMallocAsync(&sc.base, sz_order + sz_zero + sz_list + sz_bnd, st);
+    if (err != cudaSuccess) {
+        sc.base = nullptr;
+        return cuda_fail(err, "cudaMallocAsync(scratch)");
+    }
+    char *p = (char *)sc.base;
+    int32_t *order = (int32_t *)p;
+    int32_t *zero = (int32_t *)(p + sz_order);
+    int32_t *bins = zero;
+    uint32_t *counters = (uint32_t *)(zero + 2 * swg::NBINS);
+    int32_t *list_count = (int32_t *)(counters + main.C + (packed ? C32 : 0));
+    int32_t *list = (int32_t *)(p + sz_order + sz_zero);
+    int2 *bnd = chunked ? (int2 *)(p + sz_order + sz_zero + sz_list) : nullptr;
+
+    err = cudaMemsetAsync(zero, 0, sz_zero, st);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "cudaMemsetAsync(scratch)");
+    int kr = swg::launch_length_order(off, n_db, order, bins, st, sms);
+    if (kr)
+        return cuda_fail(kr, "length order kernels");
+
+    swg::BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.A = prof->A;
+    a.qlen = prof->qlen;
+    a.db = db;
+    a.off = off;
+    a.order = order;
+    a.n_work = n_db;
+    a.o = o;
+    a.e = e;
+    a.bnd = bnd;
+    a.scores = scores;
+    a.prof = main_prof;
+    a.nchunks = main.C;
+    for (int c = 0; c < main.C; ++c) {
+        a.chunk = c;
+        a.counter = counters + c;
+        kr = launch_plan(main, lazy, a, sms, st);
+        if (kr)
+            return cuda_fail(kr, "batch kernel launch");
+    }
+    if (packed) {
+        const int32_t thresh = (lane == SW_LANE_I16X2 ? 32767 : 127) - std::max(prof->maxM, 0);
+        kr = swg::launch_flag_overflow(scores, n_db, thresh, list, list_count, st, sms);
+        if (kr)
+            return cuda_fail(kr, "overflow flag kernel");
+        a.prof = prof->d_prof32;
+        a.nchunks = C32;
+        a.order = list;
+        a.n_work = n_db;
+        a.n_work_dev = list_count;
+        for (int c = 0; c < C32; ++c) {
+            a.chunk = c;
+            a.counter = counters + main.C + c;
+            kr = launch_plan(prof->plan32, false, a, sms, st);
+            if (kr)
+                return cuda_fail(kr, "rescore kernel launch");
+        }
+    }
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sw_last_error(void) { return g_err.c_str(); }
+
+const char *sw_version(void) { return "0.1.0"; }
+
+int sw_profile_build(const uint8_t *query, int32_t qlen, const int8_t *subst_matrix, int32_t alphabet,
+                     int32_t lane_type, void *cuda_stream, sw_profile **out)
+{
+    if (!out)
+        return fail(SW_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (qlen < 0)
+        return fail(SW_ERR_INVALID, "qlen < 0 (%d)", qlen);
+    if (qlen > 0 && !query)
+        return fail(SW_ERR_INVALID, "query is NULL");
+    if (alphabet < 1 || alphabet > 32)
+        return fail(SW_ERR_INVALID, "alphabet must be in 1..32 (got %d)", alphabet);
+    if (!subst_matrix)
+        return fail(SW_ERR_INVALID, "subst_matrix is NULL");
+    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I8X4)
+        return fail(SW_ERR_INVALID, "unknown lane_type %d", lane_type);
+    for (int32_t i = 0; i < qlen; ++i)
+        if (query[i] >= alphabet)
+            return fail(SW_ERR_INVALID, "query residue %d at %d is >= alphabet %d", query[i], i, alphabet);
+
+    sw_profile *pf = new sw_profile();
+    pf->qlen = qlen;
+    pf->A = alphabet;
+    pf->maxM = -128;
+    pf->minM = 127;
+    for (int i = 0; i < alphabet * alphabet; ++i) {
+        pf->maxM = std::max<int32_t>(pf->maxM, subst_matrix[i]);
+        pf->minM = std::min<int32_t>(pf->minM, subst_matrix[i]);
+    }
+    int lane = lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type;
+    pf->lane = lane;
+    pf->plan = choose_plan(qlen, lane);
+    pf->plan32 = choose_plan(qlen, SW_LANE_I32);
+    cudaGetDevice(&pf->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    auto cleanup = [&](int code) {
+        sw_profile_free(pf);
+        return code;
+    };
+    const size_t qbytes = (size_t)std::max(qlen, 1);
+    const size_t mbytes = (size_t)alphabet * alphabet;
+    const size_t pbytes = (size_t)pf->plan.C * alphabet * pf->plan.L * pf->plan.S;
+    const size_t p32bytes = (size_t)pf->plan32.C * alphabet * pf->plan32.L * pf->plan32.S;
+    cudaError_t err = cudaMalloc(&pf->d_query, qbytes);
+    if (err == cudaSuccess)
+        err = cudaMalloc(&pf->d_M, mbytes);
+    if (err == cudaSuccess && pbytes)
+        err = cudaMalloc(&pf->d_prof, pbytes);
+    if (err == cudaSuccess && p32bytes) {
+        if (lane == SW_LANE_I32)
+            pf->d_prof32 = pf->d_prof;
+        else
+            err = cudaMalloc(&pf->d_prof32, p32bytes);
+    }
+    if (err != cudaSuccess)
+        return cleanup(cuda_fail(err, "cudaMalloc(profile)"));
+    if (qlen > 0)
+        err = cudaMemcpyAsync(pf->d_query, query, (size_t)qlen, cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(pf->d_M, subst_matrix, mbytes, cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess)
+        return cleanup(cuda_fail(err, "profile upload"));
+    if (qlen > 0) {
+        int kr = swg::launch_profile_build(pf->d_query, qlen, pf->d_M, alphabet, pf->plan, pf->d_prof, st);
+        if (!kr && lane != SW_LANE_I32)
+            kr = swg::launch_profile_build(pf->d_query, qlen, pf->d_M, alphabet, pf->plan32, pf->d_prof32, st);
+        if (kr)
+            return cleanup(cuda_fail(kr, "profile build kernel"));
+    }
+    *out = pf;
+    return SW_OK;
+}
+
+int sw_profile_free(sw_profile *prof)
+{
+    if (!prof)
+        return SW_OK;
+    if (prof->d_prof32 && prof->d_prof32 != prof->d_prof)
+        cudaFree(prof->d_prof32);
+    if (prof->d_prof)
+        cudaFree(prof->d_prof);
+    if (prof->d_M)
+        cudaFree(prof->d_M);
+    if (prof->d_query)
+        cudaFree(prof->d_query);
+    delete prof;
+    return SW_OK;
+}
+
+int sw_profile_plan(const sw_profile *prof, int32_t *lanes, int32_t *seg_len, int32_t *chunks, int32_t *lane_type)
+{
+    if (!prof)
+        return fail(SW_ERR_INVALID, "profile is NULL");
+    if (lanes)
+        *lanes = prof->plan.L;
+    if (seg_len)
+        *seg_len = prof->plan.S;
+    if (chunks)
+        *chunks = prof->plan.C;
+    if (lane_type)
+        *lane_type = prof->lane;
+    return SW_OK;
+}
+
+int sw_align_batch(const sw_profile *prof, const uint8_t *db_residues, const int64_t *db_offsets, int64_t n_db,
+                   int32_t gap_open, int32_t gap_extend, int32_t *scores_out, void *cuda_stream)
+{
+    return align_impl(prof, db_residues, db_offsets, n_db, gap_open, gap_extend, scores_out, cuda_stream, false);
+}
+
+int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues, const int64_t *db_offsets,
+                         int64_t n_db, int32_t gap_open, int32_t gap_extend, int32_t *scores_out,
+                         void *cuda_stream)
+{
+    return align_impl(prof, db_residues, db_offsets, n_db, gap_open, gap_extend, scores_out, cuda_stream, true);
+}
+
+int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
+                   int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
+                   int32_t gap_extend, int32_t lane_type, int32_t *scores_out, void *cuda_stream)
+{
+    (void)q;
+    (void)q_off;
+    (void)r;
+    (void)r_off;
+    (void)n_pairs;
+    (void)subst_matrix;
+    (void)alphabet;
+    (void)gap_open;
+    (void)gap_extend;
+    (void)lane_type;
+    (void)scores_out;
+    (void)cuda_stream;
+    return fail(SW_ERR_INVALID, "sw_align_pairs: not built yet");
+}
+
+int sw_stream_sync(void *cuda_stream, int64_t timeout_ms)
+{
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t err = cudaStreamQuery(st);
+        if (err == cudaSuccess)
+            return SW_OK;
+        if (err != cudaErrorNotReady)
+            return cuda_fail(err, "cudaStreamQuery");
+        const auto ms =
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (ms >= timeout_ms)
+            return fail(SW_ERR_TIMEOUT, "stream still busy after %lld ms", (long long)timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_second, void *cuda_stream)
+{
+    if (!cells_per_second)
+        return fail(SW_ERR_INVALID, "cells_per_second is NULL");
+    if (lane_type < SW_LANE_I32 || lane_type > SW_LANE_I8X4)
+        return fail(SW_ERR_INVALID, "lane_type must be I32, I16X2 or I8X4");
+    if (iters < 1)
+        return fail(SW_ERR_INVALID, "iters must be >= 1");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = num_sms_of(dev);
+    double lane_ops = 0;
+    float ms = 0;
+    const int op = lane_type - 1;
+    int kr = swg::run_int_peak(op, sms * 8, 256, iters, &lane_ops, &ms, (cudaStream_t)cuda_stream);
+    if (kr)
+        return cuda_fail(kr, "cell-rate probe");
+    const double cells_per_op = lane_type == SW_LANE_I32 ? 1.0 : (lane_type == SW_LANE_I16X2 ? 2.0 : 4.0);
+    *cells_per_second = ms > 0 ? lane_ops / 6.0 * cells_per_op / (ms * 1e-3) : 0.0;
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// Auxiliary kernels: striped profile build, length-binned work order,
+// overflow flagging, and the integer-throughput probe used for the ALU
+// roofline.
+#include <stdint.h>
+
+#include "sw_internal.h"
+#include "sw_lanes.cuh"
+
+namespace swg {
+
+// ---------------------------------------------------------------------------
+// Striped query profile (Alg. 1 "vprofile"): for chunk c, residue a, lane l,
+// segment index j the score M[Q[c*L*S + l*S + j]][a]; 0 past the query end
+// (the batch kernel makes those positions inert when it stages the chunk).
+// Layout [C][A][L][S] int8.
+// ---------------------------------------------------------------------------
+__global__ void profile_build_kernel(const uint8_t *__restrict__ query, int32_t qlen, const int8_t *__restrict__ M,
+                                     int32_t A, int32_t L, int32_t S, int32_t C, int8_t *__restrict__ prof)
+{
+    const int64_t QC = (int64_t)L * S;
+    const int64_t total = (int64_t)C * A * QC;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / (A * QC);
+        const int64_t rem = i - c * A * QC;
+        const int a = (int)(rem / QC);
+        const int64_t pos = rem - (int64_t)a * QC;  // l*S + j
+        const int64_t q = c * QC + pos;
+        prof[i] = q < qlen ? M[(int)query[q] * A + a] : (int8_t)0;
+    }
+}
+
+int launch_profile_build(const uint8_t *d_query, int32_t qlen, const int8_t *d_M, int32_t A, const Plan &pl,
+                         int8_t *d_prof, cudaStream_t st)
+{
+    const int64_t total = (int64_t)pl.C * A * pl.L * pl.S;
+    if (total == 0)
+        return (int)cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 4096)
+        blocks = 4096;
+    profile_build_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_query, qlen, d_M, A, pl.L, pl.S, pl.C, d_prof);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Length-binned order, longest bin first.  Key: 0 for empty, else
+// 1 + 4*floor(log2 n) + the two bits below the leading one (quarter-octave
+// bins).  Within a bin the order is whatever the atomics give; every
+// sequence's score is independent of the order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int length_key(int64_t n)
+{
+    if (n <= 0)
+        return 0;
+    const unsigned v = (unsigned)min(n, (int64_t)0x7fffffff);
+    const int lg = 31 - __clz(v);
+    const int frac = lg >= 2 ? (int)((v >> (lg - 2)) & 3u) : 0;
+    return 1 + 4 * lg + frac;
+}
+
+__global__ void length_hist_kernel(const int64_t *__restrict__ off, int64_t n, int32_t *hist)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[length_key(off[i + 1] - off[i])], 1);
+}
+
+// one block of NBINS threads: cursor[k] = number of sequences in bins > k
+__global__ void length_scan_kernel(const int32_t *hist, int32_t *cursor)
+{
+    __shared__ int32_t h[NBINS];
+    const int k = threadIdx.x;
+    h[k] = hist[k];
+    __syncthreads();
+    int32_t s = 0;
+    for (int b = k + 1; b < NBINS; ++b)
+        s += h[b];
+    cursor[k] = s;
+}
+
+__global__ void length_scatter_kernel(const int64_t *__restrict__ off, int64_t n, int32_t *cursor,
+                                      int32_t *__restrict__ order)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int pos = atomicAdd(&cursor[length_key(off[i + 1] - off[i])], 1);
+        order[pos] = (int32_t)i;
+    }
+}
+
+int launch_length_order(const int64_t *off, int64_t n, int32_t *order, int32_t *bins, cudaStream_t st, int num_sms)
+{
+    if (n <= 0)
+        return (int)cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms * 8)
+        blocks = (int64_t)num_sms * 8;
+    length_hist_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n, bins);
+    length_scan_kernel<<<1, NBINS, 0, st>>>(bins, bins + NBINS);
+    length_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n, bins + NBINS, order);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Overflow flagging of packed-lane results (the paper does not cover lane
+// overflow).  A packed lane is exact until some H + M exceeds the lane
+// ceiling; that H was an exact value already folded into the alignment's
+// maximum, so any alignment whose lane result reached ceiling - max(M) is
+// listed for an int32 rescore.
+// ---------------------------------------------------------------------------
+__global__ void flag_overflow_kernel(const int32_t *__restrict__ scores, int64_t n, int32_t thresh, int32_t *list,
+                                     int32_t *count)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (scores[i] >= thresh)
+            list[atomicAdd(count, 1)] = (int32_t)i;
+}
+
+int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32_t *list, int32_t *count,
+                         cudaStream_t st, int num_sms)
+{
+    if (n <= 0)
+        return (int)cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms * 8)
+        blocks = (int64_t)num_sms * 8;
+    flag_overflow_kernel<<<(unsigned)blocks, 256, 0, st>>>(scores, n, thresh, list, count);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Integer-throughput probe.  Each thread updates K independent cells with the
+// exact per-cell instruction sequence of the batch kernel's plain pass (no
+// loads, no shuffles), so the measured rate is the ALU ceiling of the cell
+// update for that lane type.  op 0: int32 cells, 1: s16x2, 2: s8x4.
+// ---------------------------------------------------------------------------
+template <class LT>
+__global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, int *sink)
+{
+    using T = typename LT::T;
+    constexpr int K = 16;
+    T Ho[K], E[K];
+    const T negO = LT::splat(-11), negE = LT::splat(-1);
+    T P0 = LT::splat((seed + threadIdx.x) & 7), P1 = LT::splat(((seed >> 3) + threadIdx.x) & 7);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        Ho[j] = LT::splat((j + threadIdx.x) & 15);
+        E[j] = LT::zero();
+    }
+    T mx = LT::zero();
+    for (int it = 0; it < iters; ++it) {
+        T hd = Ho[K - 1];
+        T F = LT::zero();
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const T h = LT::addmax_relu(hd, (j & 1) ? P1 : P0, E[j]);
+            hd = Ho[j];
+            const T ho = LT::add(h, negO);
+            Ho[j] = LT::addmax(F, negO, ho);
+            E[j] = LT::addmax(E[j], negE, Ho[j]);
+            F = LT::addmax(F, negE, ho);
+            mx = LT::max2(mx, h);
+        }
+        const T t = P0;
+        P0 = P1;
+        P1 = t;
+    }
+    int acc = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        acc ^= (int)Ho[j] ^ (int)E[j];
+    acc ^= (int)mx;
+    if (acc == 0x7fffffff)
+        sink[0] = acc;
+}
+
+int run_int_peak(int op, int blocks, int threads, int iters, double *lane_ops, float *ms, cudaStream_t st)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int *sink = nullptr;
+    cudaError_t err = cudaMallocAsync((void **)&sink, sizeof(int), st);
+    if (err != cudaSuccess)
+        return (int)err;
+    auto go = [&](void) {
+        if (op == 0)
+            cell_peak_kernel<LaneI32><<<blocks, threads, 0, st>>>(iters, 12345, sink);
+        else if (op == 1)
+            cell_peak_kernel<LaneI16x2><<<blocks, threads, 0, st>>>(iters, 12345, sink);
+        else
+            cell_peak_kernel<LaneI8x4><<<blocks, threads, 0, st>>>(iters, 12345, sink);
+    };
+    go();  // warm-up
+    cudaEventRecord(a, st);
+    go();
+    cudaEventRecord(b, st);
+    err = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (err == cudaSuccess)
+        err = cudaEventElapsedTime(&t, a, b);
+    cudaFreeAsync(sink, st);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (err != cudaSuccess)
+        return (int)err;
+    // 6 instructions per cell-update (addmax_relu, add, 3 x addmax, max)
+    *lane_ops = 6.0 * 16.0 * (double)iters * (double)blocks * (double)threads;
+    *ms = t;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace swg

@@ -1,0 +1,73 @@
+// Internal declarations shared by the host API (sw_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swg {
+
+enum LaneKind { LK_I32 = 1, LK_I16X2 = 2, LK_I8X4 = 3 };
+
+// One layout of the striped query: L lanes per alignment, S positions per
+// lane (the paper's p and segLen), C query chunks of L*S positions each.
+struct Plan {
+    int L = 0, S = 0, C = 0, lane = 0;
+};
+
+// Parameters of one launch of the batch kernel (one query chunk).
+struct BatchArgs {
+    const int8_t *prof;       // raw striped profile of this plan: [C][A][L][S] int8 (M values)
+    int32_t A;                // alphabet size; profile row A is the inert "no residue" row
+    int32_t qlen;
+    int32_t chunk, nchunks;
+    const uint8_t *db;
+    const int64_t *off;       // db offsets, n+1
+    const int32_t *order;     // sequence ids in processing order (may be null: identity)
+    int64_t n_work;           // entries of order to process
+    const int32_t *n_work_dev;  // if set, the number of entries is read here instead
+    int32_t o, e;
+    int2 *bnd;                // boundary rows between chunks: per sequence, index off[seq]+r
+    int32_t *scores;          // per sequence
+    uint32_t *counter;        // work counter, zero at launch
+    unsigned long long *lazy_steps;  // optional statistics of the lazy-F loop
+};
+
+// Parameters of the pair kernel (each pair has its own query).
+struct PairArgs {
+    const uint8_t *q;
+    const int64_t *q_off;
+    const uint8_t *r;
+    const int64_t *r_off;
+    int64_t n_pairs;
+    const int32_t *order;       // optional pair ids to process (rescore list)
+    const int32_t *n_work_dev;  // optional device count of order entries
+    int32_t A, o, e;
+    int8_t M[32 * 32];          // substitution matrix [query][reference]
+    int32_t *scores;
+    uint32_t *counter;
+};
+
+// batch launchers (sw_kernels_*.cu).  Return a cudaError_t.
+int launch_batch(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
+bool plan_supported(const Plan &pl, bool lazy);
+int launch_pairs(int lane, int qmax, const PairArgs &a, int num_sms, cudaStream_t st);
+
+// aux kernels (sw_aux.cu)
+int launch_profile_build(const uint8_t *d_query, int32_t qlen, const int8_t *d_M, int32_t A, const Plan &pl,
+                         int8_t *d_prof, cudaStream_t st);
+// Length-binned processing order, longest first: order[n] of sequence ids.
+// scratch: 2*NBINS int32 of zeroed scratch (histogram, cursors).
+constexpr int NBINS = 128;
+int launch_length_order(const int64_t *off, int64_t n, int32_t *order, int32_t *bins, cudaStream_t st,
+                        int num_sms);
+// Sequences whose score reached thresh -> list (count in *count, zero at launch).
+int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32_t *list, int32_t *count,
+                         cudaStream_t st, int num_sms);
+int launch_flag_overflow_pairs(const int32_t *scores, const int64_t *q_off, int64_t n, int32_t thresh_base,
+                               int32_t *list, int32_t *count, cudaStream_t st, int num_sms);
+
+// Integer-op throughput probe for the ALU roofline: 'op' selects the
+// instruction stream; returns ops executed (lane-ops) and elapsed ms.
+int run_int_peak(int op, int blocks, int threads, int iters, double *lane_ops, float *ms, cudaStream_t st);
+
+}  // namespace swg

@@ -1,0 +1,19 @@
+// s16x2-lane instantiations of the scan-F kernel (two alignments per register).
+#include "sw_launch.cuh"
+
+namespace swg {
+
+int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
+{
+#define SWG_CASE(LL, SS)                          \
+    if (pl.L == LL && pl.S == SS)                 \
+        return launch_batch_inst<LaneI16x2, LL, SS, false>(a, num_sms, st);
+    SWG_CASE(8, 8)
+    SWG_CASE(16, 8)
+    SWG_CASE(32, 8)
+    SWG_CASE(32, 16)
+#undef SWG_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace swg

@@ -1,0 +1,21 @@
+// int32-lane instantiations: scan-F (Alg. 6) and lazy-F (Alg. 1).
+#include "sw_launch.cuh"
+
+namespace swg {
+
+int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st)
+{
+#define SWG_CASE(LL, SS)                                                              \
+    if (pl.L == LL && pl.S == SS)                                                     \
+        return lazy ? launch_batch_inst<LaneI32, LL, SS, true>(a, num_sms, st)        \
+                    : launch_batch_inst<LaneI32, LL, SS, false>(a, num_sms, st);
+    SWG_CASE(4, 8)
+    SWG_CASE(8, 8)
+    SWG_CASE(16, 8)
+    SWG_CASE(32, 8)
+    SWG_CASE(32, 16)
+#undef SWG_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace swg

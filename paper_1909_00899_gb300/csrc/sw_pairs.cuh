@@ -1,0 +1,147 @@
+// Pair kernel: n independent alignments, each with its own query (reads
+// against their own reference windows).  Each group of L lanes takes CELLS
+// pairs, writes their striped profiles into its own slice of shared memory
+// (biased by +o, straight from the query residues and the substitution
+// matrix held in the launch parameters), then runs the same per-column
+// scan-F core as the batch kernel.  Pairs arrive pre-sorted into
+// query-length classes so that one launch covers queries of at most L*S
+// positions (single chunk).
+#pragma once
+#include "sw_batch.cuh"
+
+namespace swg {
+
+template <class LT, int L, int S>
+__global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const int32_t *__restrict__ list,
+                                                       const int32_t *__restrict__ count_dev)
+{
+    using T = typename LT::T;
+    using Elem = typename LT::Elem;
+    constexpr int CELLS = LT::CELLS;
+    constexpr int V = LT::VEC;
+    constexpr int SP = SegPad<S, V>::value;
+    constexpr int G = 32 / L;
+    constexpr unsigned FULL = 0xffffffffu;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int A = p.A;
+    const int cell_elems = (A + 1) * L * SP;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const int gid = (threadIdx.x >> 5) * G + grp;
+    Elem *gprof = reinterpret_cast<Elem *>(smem_raw) + (size_t)gid * CELLS * cell_elems;
+    const Elem *pbase[CELLS];
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c)
+        pbase[c] = gprof + c * cell_elems;
+
+    const int64_t n_work = count_dev ? (int64_t)(*count_dev) : p.n_pairs;
+    const int64_t units = (n_work + CELLS - 1) / CELLS;
+    unsigned long long unused = 0;
+
+    for (;;) {
+        unsigned int ubase = 0;
+        if (lane == 0)
+            ubase = atomicAdd(p.counter, (unsigned int)G);
+        ubase = __shfl_sync(FULL, ubase, 0);
+        if ((int64_t)ubase >= units)
+            break;
+        const int64_t unit = (int64_t)ubase + grp;
+        int pid[CELLS];
+        int64_t start[CELLS];
+        int len[CELLS];
+        int my_n = 0;
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) {
+            const int64_t w = unit * CELLS + c;
+            const bool ok = unit < units && w < n_work;
+            pid[c] = ok ? (list ? list[w] : (int)w) : -1;
+            int64_t qs = 0;
+            int ql = 0;
+            if (ok) {
+                qs = p.q_off[pid[c]];
+                ql = (int)(p.q_off[pid[c] + 1] - qs);
+                start[c] = p.r_off[pid[c]];
+                len[c] = (int)(p.r_off[pid[c] + 1] - start[c]);
+            } else {
+                start[c] = 0;
+                len[c] = 0;
+            }
+            if (ql == 0)
+                len[c] = 0;  // empty query: score 0
+            my_n = max(my_n, len[c]);
+            // this cell's striped profile: lane gl fills segment positions
+            Elem *dst = gprof + c * cell_elems;
+            for (int pos = gl; pos < L * SP; pos += L) {
+                const int l = pos / SP;
+                const int j = pos - l * SP;
+                const int qp = l * S + j;
+                int code = -1;
+                if (j < S && qp < ql) {
+                    code = (int)p.q[qs + qp];
+                    if (code >= A)
+                        code = -1;  // unknown query residue: never scores
+                }
+#pragma unroll 4
+                for (int a = 0; a <= A; ++a) {
+                    int v = LT::PAD;
+                    if (code >= 0 && a < A)
+                        v = (int)p.M[code * A + a] + p.o;
+                    dst[((a * (SP / V) + j / V) * L + l) * V + (j % V)] = (Elem)v;
+                }
+            }
+        }
+        __syncwarp(FULL);
+        const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
+        const T mx = striped_unit<LT, L, S, false>(pbase, p.r, start, len, ncols, A, p.o, p.e, false, false,
+                                                   nullptr, gl, unused);
+        if (gl == 0) {
+#pragma unroll
+            for (int c = 0; c < CELLS; ++c)
+                if (pid[c] >= 0)
+                    p.scores[pid[c]] = LT::get(mx, c);
+        }
+        __syncwarp(FULL);  // profiles are rewritten by the next unit
+    }
+}
+
+// Shared memory of one warp: CELLS profiles per group, 32 / L groups.
+template <class LT, int S>
+constexpr size_t pair_smem_per_warp(int A)
+{
+    return (size_t)32 * LT::CELLS * (A + 1) * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
+}
+
+template <class LT, int L, int S>
+int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
+                      int num_sms, cudaStream_t st)
+{
+    auto kern = sw_pairs_kernel<LT, L, S>;
+    const size_t per_warp = pair_smem_per_warp<LT, S>(a.A);
+    int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
+    const size_t smem = per_warp * warps;
+    if (smem > 200 * 1024)
+        return (int)cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return (int)err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (err != cudaSuccess)
+        return (int)err;
+    if (per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    const int64_t units = (n_hint + LT::CELLS - 1) / LT::CELLS;
+    const int64_t per_block = (int64_t)warps * (32 / L);
+    const int64_t need = (units + per_block - 1) / per_block;
+    if (need < grid)
+        grid = need;
+    if (grid < 1)
+        return (int)cudaSuccess;
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(a, list, count_dev);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace swg

@@ -1,0 +1,206 @@
+"""ctypes binding of libsw_gb300.so (include/sw_gb300.h), same names as the
+C entry points.  Argument marshalling only: tensors are passed by
+``data_ptr()``, streams by ``torch.cuda.Stream.cuda_stream``; every compute
+step runs in the library's CUDA kernels.
+
+The library is loaded on first use; if it is missing or cannot be loaded the
+call raises (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsw_gb300.so")
+
+SW_OK = 0
+SW_ERR_INVALID = -1
+SW_ERR_CUDA = -2
+SW_ERR_NOMEM = -3
+SW_ERR_TIMEOUT = -4
+SW_ERR_RANGE = -5
+
+SW_LANE_AUTO = 0
+SW_LANE_I32 = 1
+SW_LANE_I16X2 = 2
+SW_LANE_I8X4 = 3
+
+# every function declared in include/sw_gb300.h
+EXPORTS = (
+    "sw_profile_build", "sw_profile_free", "sw_profile_plan", "sw_align_batch",
+    "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
+    "sw_probe_cell_rate", "sw_version",
+)
+
+
+class SwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+def lib():
+    """Load the library (raises OSError if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libsw_gb300.so is not built (run __graft_entry__.build()); "
+                          "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        L.sw_profile_build.restype = ctypes.c_int
+        L.sw_profile_build.argtypes = [_vp, _i32, _vp, _i32, _i32, _vp, ctypes.POINTER(_vp)]
+        L.sw_profile_free.restype = ctypes.c_int
+        L.sw_profile_free.argtypes = [_vp]
+        L.sw_profile_plan.restype = ctypes.c_int
+        L.sw_profile_plan.argtypes = [_vp] + [ctypes.POINTER(_i32)] * 4
+        for name in ("sw_align_batch", "sw_align_lazyf_batch"):
+            f = getattr(L, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp]
+        L.sw_align_pairs.restype = ctypes.c_int
+        L.sw_align_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
+        L.sw_stream_sync.restype = ctypes.c_int
+        L.sw_stream_sync.argtypes = [_vp, _i64]
+        L.sw_last_error.restype = ctypes.c_char_p
+        L.sw_last_error.argtypes = []
+        L.sw_version.restype = ctypes.c_char_p
+        L.sw_version.argtypes = []
+        L.sw_probe_cell_rate.restype = ctypes.c_int
+        L.sw_probe_cell_rate.argtypes = [_i32, _i32, ctypes.POINTER(ctypes.c_double), _vp]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != SW_OK:
+        raise SwError(rc, lib().sw_last_error().decode(errors="replace"))
+    return rc
+
+
+def _stream(stream):
+    """A torch stream, an int handle or None (current torch stream)."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype_name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError("expected dtype %s, got %s" % (dtype_name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+class Profile:
+    """Owns a device profile built by sw_profile_build."""
+
+    def __init__(self, query, subst_matrix, lane_type=SW_LANE_AUTO, stream=None):
+        q = np.ascontiguousarray(query, dtype=np.uint8)
+        M = np.ascontiguousarray(subst_matrix, dtype=np.int8)
+        if M.ndim != 2 or M.shape[0] != M.shape[1]:
+            raise ValueError("subst_matrix must be square")
+        self.qlen = int(q.size)
+        self.alphabet = int(M.shape[0])
+        h = _vp()
+        _check(lib().sw_profile_build(q.ctypes.data if q.size else None, self.qlen,
+                                      M.ctypes.data, self.alphabet, lane_type,
+                                      _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def plan(self):
+        vals = [_i32() for _ in range(4)]
+        _check(lib().sw_profile_plan(self._h, *[ctypes.byref(v) for v in vals]))
+        return dict(lanes=vals[0].value, seg_len=vals[1].value, chunks=vals[2].value,
+                    lane_type=vals[3].value)
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().sw_profile_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sw_profile_build(query, subst_matrix, lane_type=SW_LANE_AUTO, stream=None):
+    return Profile(query, subst_matrix, lane_type, stream)
+
+
+def sw_profile_free(profile):
+    profile.free()
+
+
+def _align(fn, profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream):
+    n_db = int(db_offsets.numel()) - 1
+    if n_db < 0:
+        raise ValueError("db_offsets needs n_db + 1 entries")
+    if scores_out.numel() < n_db:
+        raise ValueError("scores_out too small")
+    _check(fn(profile.handle, _dev_ptr(db_residues, "uint8"), _dev_ptr(db_offsets, "int64"),
+              n_db, int(gap_open), int(gap_extend), _dev_ptr(scores_out, "int32"), _stream(stream)))
+    return scores_out
+
+
+def sw_align_batch(profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream=None):
+    """Scan-F (Alg. 6) scores of profile's query against every db sequence."""
+    return _align(lib().sw_align_batch, profile, db_residues, db_offsets, gap_open, gap_extend,
+                  scores_out, stream)
+
+
+def sw_align_lazyf_batch(profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream=None):
+    """Lazy-F (Alg. 1) scores, the plain-method comparison."""
+    return _align(lib().sw_align_lazyf_batch, profile, db_residues, db_offsets, gap_open, gap_extend,
+                  scores_out, stream)
+
+
+def sw_align_pairs(q, q_off, r, r_off, subst_matrix, gap_open, gap_extend, scores_out,
+                   lane_type=SW_LANE_AUTO, stream=None):
+    """Pair k: q[q_off[k]:q_off[k+1]] against r[r_off[k]:r_off[k+1]]."""
+    M = np.ascontiguousarray(subst_matrix, dtype=np.int8)
+    n = int(q_off.numel()) - 1
+    if int(r_off.numel()) - 1 != n:
+        raise ValueError("q_off and r_off must have the same length")
+    _check(lib().sw_align_pairs(_dev_ptr(q, "uint8"), _dev_ptr(q_off, "int64"), _dev_ptr(r, "uint8"),
+                                _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
+                                int(gap_open), int(gap_extend), int(lane_type),
+                                _dev_ptr(scores_out, "int32"), _stream(stream)))
+    return scores_out
+
+
+def sw_stream_sync(stream=None, timeout_ms=60_000):
+    return _check(lib().sw_stream_sync(_stream(stream), int(timeout_ms)))
+
+
+def sw_last_error():
+    return lib().sw_last_error().decode(errors="replace")
+
+
+def sw_version():
+    return lib().sw_version().decode()
+
+
+def sw_probe_cell_rate(lane_type=SW_LANE_I32, iters=4096, stream=None):
+    out = ctypes.c_double(0.0)
+    _check(lib().sw_probe_cell_rate(int(lane_type), int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value

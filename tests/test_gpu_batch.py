@@ -1,0 +1,180 @@
+"""GPU parity of sw_align_batch (scan-F, every lane type) and
+sw_align_lazyf_batch against the CPU oracle: bit-exact int32 scores."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_00899_gb300 import synth
+
+from helpers import db_to_dev, gap_adversary, pack_list
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+LANES = ["i32", "i16x2", "i8x4", "auto", "lazyf"]
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from paper_1909_00899_gb300 import sw as swmod
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    swmod.lib()
+    return swmod
+
+
+def run(sw, kind, query, M, db_d, off_d, o, e):
+    lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i8x4": sw.SW_LANE_I8X4,
+            "auto": sw.SW_LANE_AUTO, "lazyf": sw.SW_LANE_I32}[kind]
+    prof = sw.Profile(query, M, lane)
+    n = off_d.numel() - 1
+    out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    if kind == "lazyf":
+        sw.sw_align_lazyf_batch(prof, db_d, off_d, o, e, out)
+    else:
+        sw.sw_align_batch(prof, db_d, off_d, o, e, out)
+    torch.cuda.synchronize()
+    res = out[:n].cpu().numpy()
+    prof.free()
+    return res
+
+
+@pytest.mark.parametrize("kind", LANES)
+def test_protein_query256_vs_1000(sw, kind):
+    """One protein query of 256 vs 1000 sequences of length U{50..500}."""
+    w = synth.workload_protein_small()
+    db_d, off_d = db_to_dev(w["db"], w["off"])
+    want = oracle.gotoh_batch(w["query"], w["db"], w["off"], w["M"], w["o"], w["e"])
+    got = run(sw, kind, w["query"], w["M"], db_d, off_d, w["o"], w["e"])
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", LANES)
+def test_query_lengths_span_plans_and_chunks(sw, kind):
+    """Query lengths around every plan boundary (32/64/128/256/512 positions)
+    and multi-chunk queries, against a ragged db with empty and 1-residue
+    sequences."""
+    rng = np.random.default_rng(1001)
+    M = synth.protein_matrix(rng)
+    lens = np.concatenate([[0, 1, 2, 3, 0, 17], rng.integers(1, 700, 120)])
+    db, off = synth.pack(lens.astype(np.int64), rng, 20)
+    db_d, off_d = db_to_dev(db, off)
+    for qlen in (1, 7, 31, 33, 64, 100, 129, 255, 257, 511, 512, 513, 1100, 1600):
+        q = synth.residues(rng, qlen, 20)
+        want = oracle.gotoh_batch(q, db, off, M, 11, 1)
+        got = run(sw, kind, q, M, db_d, off_d, 11, 1)
+        np.testing.assert_array_equal(got, want, err_msg="qlen=%d" % qlen)
+
+
+@pytest.mark.parametrize("kind", LANES)
+def test_gap_adversary_dna(sw, kind):
+    """Long query-side insertions (vertical gaps through many segments) with
+    DNA scoring; each query is aligned against every reference."""
+    rng = np.random.default_rng(1002)
+    M = synth.dna_matrix()
+    queries, refs = gap_adversary(rng, 4, 40)
+    db, off = pack_list(refs)
+    db_d, off_d = db_to_dev(db, off)
+    for q in queries[:6]:
+        want = oracle.gotoh_batch(q, db, off, M, 6, 1)
+        got = run(sw, kind, q, M, db_d, off_d, 6, 1)
+        np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", LANES)
+def test_random_gap_costs(sw, kind):
+    rng = np.random.default_rng(1003)
+    M = synth.protein_matrix(rng)
+    db, off = synth.random_db(rng, 200, 20, "uniform", lo=1, hi=300)
+    db_d, off_d = db_to_dev(db, off)
+    for o, e in ((1, 0), (1, 1), (3, 3), (5, 0), (7, 2), (11, 1), (12, 12), (20, 5)):
+        q = synth.residues(rng, int(rng.integers(20, 600)), 20)
+        want = oracle.gotoh_batch(q, db, off, M, o, e)
+        got = run(sw, kind, q, M, db_d, off_d, o, e)
+        np.testing.assert_array_equal(got, want, err_msg="o=%d e=%d" % (o, e))
+
+
+@pytest.mark.parametrize("kind", LANES)
+def test_overflow_boundaries_rescored_exactly(sw, kind):
+    """Identical DNA stretches whose true score sits just below, at and above
+    the s8 (127) and s16 (32767) ceilings: packed lanes must flag them and
+    the int32 rescore must return the exact value."""
+    rng = np.random.default_rng(1004)
+    M = synth.dna_matrix()
+    base = synth.residues(rng, 33000, 4)
+    q = base[:600]
+    seqs = [base[:k] for k in (120, 121, 126, 127, 128, 129, 140, 300, 600)]
+    seqs += [synth.residues(rng, 50, 4)]
+    db, off = pack_list(seqs)
+    db_d, off_d = db_to_dev(db, off)
+    want = oracle.gotoh_batch(q, db, off, M, 6, 1)
+    assert want[3] == 127 and want[4] == 128
+    got = run(sw, kind, q, M, db_d, off_d, 6, 1)
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", ["i16x2", "auto"])
+def test_int16_ceiling(sw, kind):
+    """True scores around 32767 - max(M) and above 32767 (identical
+    sequences with a +11 diagonal) are rescored exactly."""
+    M = np.full((20, 20), -4, np.int8)
+    np.fill_diagonal(M, 11)
+    rng = np.random.default_rng(1005)
+    q = synth.residues(rng, 3100, 20)
+    seqs = [q[:k] for k in (2975, 2977, 2978, 2979, 3000, 3100)]
+    db, off = pack_list(seqs)
+    db_d, off_d = db_to_dev(db, off)
+    want = oracle.gotoh_batch(q, db, off, M, 11, 1)
+    assert want.max() > 32767
+    got = run(sw, kind, q, M, db_d, off_d, 11, 1)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_empty_inputs(sw):
+    rng = np.random.default_rng(1006)
+    M = synth.protein_matrix(rng)
+    db, off = synth.random_db(rng, 10, 20, "uniform", lo=0, hi=40)
+    db_d, off_d = db_to_dev(db, off)
+    got = run(sw, "i32", np.zeros(0, np.uint8), M, db_d, off_d, 11, 1)
+    assert (got == 0).all()
+    prof = sw.Profile(synth.residues(rng, 50, 20), M)
+    empty_off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sw.sw_align_batch(prof, db_d, empty_off, 11, 1, out)
+    torch.cuda.synchronize()
+
+
+def test_gap_cost_errors(sw):
+    rng = np.random.default_rng(1007)
+    M = synth.protein_matrix(rng)
+    db, off = synth.random_db(rng, 4, 20, "uniform", lo=5, hi=9)
+    db_d, off_d = db_to_dev(db, off)
+    prof = sw.Profile(synth.residues(rng, 50, 20), M)
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    for o, e in ((0, 0), (5, 6), (3, -1)):
+        with pytest.raises(sw.SwError) as ei:
+            sw.sw_align_batch(prof, db_d, off_d, o, e, out)
+        assert ei.value.code == sw.SW_ERR_INVALID
+
+
+def test_stream_sync_and_scores_independent_of_stream(sw):
+    rng = np.random.default_rng(1008)
+    M = synth.protein_matrix(rng)
+    db, off = synth.random_db(rng, 300, 20, "uniform", lo=10, hi=400)
+    db_d, off_d = db_to_dev(db, off)
+    q = synth.residues(rng, 300, 20)
+    s = torch.cuda.Stream()
+    prof = sw.Profile(q, M, sw.SW_LANE_AUTO, stream=s)
+    out = torch.zeros(300, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(s):
+        sw.sw_align_batch(prof, db_d, off_d, 11, 1, out, stream=s)
+    sw.sw_stream_sync(s, 30_000)
+    want = oracle.gotoh_batch(q, db, off, M, 11, 1)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_cell_rate_probe_runs(sw):
+    for lane in (sw.SW_LANE_I32, sw.SW_LANE_I16X2, sw.SW_LANE_I8X4):
+        r = sw.sw_probe_cell_rate(lane, 256)
+        assert r > 1e9
