@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-lazyf", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU work of the oracle baseline sample")
+    ap.add_argument("--qlens", default=",".join(map(str, QLENS)),
+                    help="comma-separated query lengths (profiling cases)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only: no oracle check, lazy-F, e2e, probe or CPU baseline")
     return ap.parse_args()
 
 
@@ -193,6 +197,11 @@ def main():
     from paper_1909_00899_gb300 import build as libbuild
     from paper_1909_00899_gb300 import sw, synth
 
+    global QLENS
+    QLENS = tuple(int(x) for x in args.qlens.split(","))
+    if args.quick:
+        args.no_cpu_baseline = True
+        args.no_lazyf = True
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -204,6 +213,9 @@ def main():
 
     w = synth.workload_protein_scale(n_db=args.n_db, qlens=QLENS)
     M, o, e = w["M"], w["o"], w["e"]
+    workload = WORKLOAD if (QLENS, args.n_db) == ((128, 512, 2048, 5000), 100_000) else (
+        "protein queries m in {%s} vs %d db seqs, log-normal lengths (median 300, sigma 0.76, "
+        "clip [20,35000]), o=11 e=1" % (",".join(map(str, QLENS)), args.n_db))
     n_db = len(w["off"]) - 1
     total_res = int(w["off"][-1])
     cells_step = sum(QLENS) * total_res
@@ -253,7 +265,7 @@ def main():
         return total_ms, per_query
 
     # correctness spot check against the oracle on a sample (not timed)
-    check = sample_check(w, outs, step, rank)
+    check = None if args.quick else sample_check(w, outs, step, rank)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -271,7 +283,7 @@ def main():
 
     # end to end through the public API: host (pinned) inputs copied in,
     # scores copied out, inside the timed region
-    e2e = run_e2e(w, lane, args, stream, cells_step)
+    e2e = None if args.quick else run_e2e(w, lane, args, stream, cells_step)
 
     # roofline of the dominant kernel (the scan-F batch kernel)
     prof0 = sw.Profile(w["queries"][-1], M, lane)
@@ -281,7 +293,7 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     peak = sms * 128 * mhz * 1e6 / (6.0 / cells_per_op) / 1e9
-    probe = sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
+    probe = None if args.quick else sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
     launches_per_step = 0
     for m in QLENS:
         pf = sw.Profile(np.zeros(m, np.uint8), M, lane)
@@ -296,7 +308,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "s16x2+int32" if cells_per_op == 2 else
         ("int32" if cells_per_op == 1 else "s8x4+int32"), "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_db": n_db, "db_residues": total_res,
+        "config": {"workload": workload, "n_db": n_db, "db_residues": total_res,
                    "cells_per_step": cells_step, "lane": args.lane, "plan_m5000": plan,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -307,7 +319,7 @@ def main():
                      "frac": gcups / world / peak, "traffic": None,
                      "peak_basis": "%d SMs x 128 int32 lane-instr/clk x %.0f MHz (median sampled) / %g instr per cell"
                                    % (sms, mhz, 6.0 / cells_per_op),
-                     "probe_gcups": probe, "frac_of_probe": gcups / world / probe},
+                     "probe_gcups": probe, "frac_of_probe": (gcups / world / probe) if probe else None},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

@@ -128,7 +128,11 @@ int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues,
  *   lane_type       SW_LANE_*: packed types flag pairs whose score may have
  *                   left the lane range and rescore them in int32
  *   scores_out      device int32[n_pairs]
- * Query lengths up to 4096 per pair.  Errors as sw_align_batch.
+ * Query lengths up to 512 per pair (SW_ERR_RANGE otherwise).  Pairs are
+ * sorted into query-length classes on the device; the class sizes are read
+ * back once (a synchronous 64-byte copy), so this call synchronises
+ * cuda_stream once and cannot be captured into a CUDA graph.  Errors as
+ * sw_align_batch.
  */
 int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r,
                    const int64_t *r_off, int64_t n_pairs,

@@ -97,6 +97,11 @@ struct Choice {
 const Choice kI32[] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {32, 16}};
 const Choice kI16[] = {{8, 8}, {16, 8}, {32, 8}, {32, 16}};
 const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
+// query-length classes of the pair kernel (one query per pair, <= 512)
+const Choice kPairI32[] = {{4, 8}, {8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
+const Choice kPairI16[] = {{8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
+const Choice kPairI8[] = {{8, 16}, {16, 10}, {16, 16}, {32, 16}};
+const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4;
 
 Plan choose_plan(int32_t qlen, int lane)
 {
@@ -134,6 +139,10 @@ bool lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan 
     if (lane == SW_LANE_I16X2) {
         // scan hop weights and decays stay far from the wrap point
         if ((int64_t)o + (int64_t)pl.L * pl.S * e + 256 > 16000)
+            return false;
+    } else {
+        // the last-position correction subtracts (S-1)*e in one saturating add
+        if ((int64_t)(pl.S - 1) * e > 127)
             return false;
     }
     return true;
@@ -424,19 +433,141 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
                    int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
                    int32_t gap_extend, int32_t lane_type, int32_t *scores_out, void *cuda_stream)
 {
-    (void)q;
-    (void)q_off;
-    (void)r;
-    (void)r_off;
-    (void)n_pairs;
-    (void)subst_matrix;
-    (void)alphabet;
-    (void)gap_open;
-    (void)gap_extend;
-    (void)lane_type;
-    (void)scores_out;
-    (void)cuda_stream;
-    return fail(SW_ERR_INVALID, "sw_align_pairs: not built yet");
+    if (n_pairs < 0)
+        return fail(SW_ERR_INVALID, "n_pairs < 0 (%lld)", (long long)n_pairs);
+    if (n_pairs > INT32_MAX - 1024)
+        return fail(SW_ERR_INVALID, "n_pairs too large (%lld)", (long long)n_pairs);
+    if (n_pairs > 0 && (!q || !q_off || !r || !r_off || !scores_out))
+        return fail(SW_ERR_INVALID, "null device pointer");
+    if (!subst_matrix)
+        return fail(SW_ERR_INVALID, "subst_matrix is NULL");
+    if (alphabet < 1 || alphabet > 32)
+        return fail(SW_ERR_INVALID, "alphabet must be in 1..32 (got %d)", alphabet);
+    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I8X4)
+        return fail(SW_ERR_INVALID, "unknown lane_type %d", lane_type);
+    if (gap_open < 1)
+        return fail(SW_ERR_INVALID, "gap_open must be >= 1 (got %d)", gap_open);
+    if (gap_extend < 0 || gap_extend > gap_open)
+        return fail(SW_ERR_INVALID, "gap_extend must satisfy 0 <= e <= gap_open (got e=%d, o=%d)", gap_extend,
+                    gap_open);
+    if (gap_open > (1 << 20))
+        return fail(SW_ERR_RANGE, "gap_open too large for int32 accumulation (%d)", gap_open);
+    if (n_pairs == 0)
+        return SW_OK;
+
+    swg::PairArgs a;
+    memset(&a, 0, sizeof(a));
+    int32_t maxM = -128;
+    for (int i = 0; i < alphabet * alphabet; ++i) {
+        a.M[i] = subst_matrix[i];
+        maxM = std::max<int32_t>(maxM, subst_matrix[i]);
+    }
+    sw_profile shape;  // only the matrix range is read by lane_fits
+    shape.maxM = maxM;
+    int lane = lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type;
+    // query-length classes of the lane type; the packed classes must fit
+    const Choice *tab = kPairI32;
+    int ncls = kPairI32N;
+    if (lane == SW_LANE_I16X2) {
+        tab = kPairI16;
+        ncls = kPairI16N;
+    } else if (lane == SW_LANE_I8X4) {
+        tab = kPairI8;
+        ncls = kPairI8N;
+    }
+    if (lane != SW_LANE_I32) {
+        Plan widest;
+        widest.L = tab[ncls - 1].L;
+        widest.S = tab[ncls - 1].S;
+        if (!lane_fits(lane, &shape, gap_open, gap_extend, widest)) {
+            lane = SW_LANE_I32;
+            tab = kPairI32;
+            ncls = kPairI32N;
+        }
+    }
+    swg::ClassTable ct;
+    ct.n = ncls;
+    for (int k = 0; k < ncls; ++k)
+        ct.q[k] = tab[k].L * tab[k].S;
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_warm(dev);
+    const int sms = num_sms_of(dev);
+    const size_t n = (size_t)n_pairs;
+    // hist, cursor (ncls + 1 each), 2 work counters and 1 list count per class
+    const size_t sz_small = align_up((size_t)(2 * (ncls + 1) + 3 * ncls) * 4);
+    const size_t sz_order = align_up(n * 4);
+    const size_t sz_list = lane != SW_LANE_I32 ? align_up(n * 4) : 0;
+    Scratch sc;
+    sc.st = st;
+    cudaError_t err = cudaMallocAsync(&sc.base, sz_small + sz_order + sz_list, st);
+    if (err != cudaSuccess) {
+        sc.base = nullptr;
+        return cuda_fail(err, "cudaMallocAsync(scratch)");
+    }
+    char *p = (char *)sc.base;
+    int32_t *hist = (int32_t *)p;
+    int32_t *cursor = hist + (ncls + 1);
+    uint32_t *counters = (uint32_t *)(cursor + (ncls + 1));  // 2 per class
+    int32_t *order = (int32_t *)(p + sz_small);
+    int32_t *list = sz_list ? (int32_t *)(p + sz_small + sz_order) : nullptr;
+    int32_t *list_count = (int32_t *)(counters + 2 * ncls);  // 1 per class
+    err = cudaMemsetAsync(p, 0, sz_small, st);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "cudaMemsetAsync(scratch)");
+    int kr = swg::launch_pair_classes(q_off, n_pairs, ct, hist, cursor, order, st, sms);
+    if (kr)
+        return cuda_fail(kr, "pair class kernels");
+    // class sizes decide the launches: one small synchronous read
+    int32_t h_hist[16] = {0};
+    err = cudaMemcpyAsync(h_hist, hist, sizeof(int32_t) * (ncls + 1), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "reading pair classes");
+    if (h_hist[ncls] > 0)
+        return fail(SW_ERR_RANGE, "%d pairs have a query longer than %d residues", h_hist[ncls], ct.q[ncls - 1]);
+
+    a.q = q;
+    a.q_off = q_off;
+    a.r = r;
+    a.r_off = r_off;
+    a.n_pairs = n_pairs;
+    a.A = alphabet;
+    a.o = gap_open;
+    a.e = gap_extend;
+    a.scores = scores_out;
+    const int32_t thresh = (lane == SW_LANE_I16X2 ? 32767 : 127) - std::max(maxM, 0);
+    int64_t begin = 0;
+    for (int k = 0; k < ncls; ++k) {
+        const int64_t cnt = h_hist[k];
+        if (cnt == 0)
+            continue;
+        const int32_t *cls = order + begin;
+        a.counter = counters + 2 * k;
+        const int lk = lane == SW_LANE_I32 ? swg::LK_I32 : (lane == SW_LANE_I16X2 ? swg::LK_I16X2 : swg::LK_I8X4);
+        kr = swg::launch_pairs(lk, tab[k].L, tab[k].S, a, cls, nullptr, cnt, sms, st);
+        if (kr)
+            return cuda_fail(kr, "pair kernel launch");
+        if (lane != SW_LANE_I32) {
+            int32_t *cl = list + begin;
+            kr = swg::launch_flag_overflow_list(scores_out, cls, cnt, thresh, cl, list_count + k, st, sms);
+            if (kr)
+                return cuda_fail(kr, "overflow flag kernel");
+            // int32 class covering the same query lengths
+            int j = 0;
+            while (j + 1 < kPairI32N && kPairI32[j].L * kPairI32[j].S < ct.q[k])
+                ++j;
+            a.counter = counters + 2 * k + 1;
+            kr = swg::launch_pairs(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, a, cl, list_count + k, cnt, sms, st);
+            if (kr)
+                return cuda_fail(kr, "rescore kernel launch");
+        }
+        begin += cnt;
+    }
+    return SW_OK;
 }
 
 int sw_stream_sync(void *cuda_stream, int64_t timeout_ms)

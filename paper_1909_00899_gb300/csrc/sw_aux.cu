@@ -126,6 +126,80 @@ int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32
     return (int)cudaGetLastError();
 }
 
+__global__ void flag_overflow_list_kernel(const int32_t *__restrict__ scores, const int32_t *__restrict__ list,
+                                          int64_t n, int32_t thresh, int32_t *out, int32_t *out_count)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t id = list[i];
+        if (scores[id] >= thresh)
+            out[atomicAdd(out_count, 1)] = id;
+    }
+}
+
+int launch_flag_overflow_list(const int32_t *scores, const int32_t *list, int64_t n, int32_t thresh, int32_t *out,
+                              int32_t *out_count, cudaStream_t st, int num_sms)
+{
+    if (n <= 0)
+        return (int)cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms * 8)
+        blocks = (int64_t)num_sms * 8;
+    flag_overflow_list_kernel<<<(unsigned)blocks, 256, 0, st>>>(scores, list, n, thresh, out, out_count);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Query-length classes of the pair kernel (counting sort by class).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pair_class(int64_t qlen, const ClassTable &t)
+{
+    for (int k = 0; k < t.n; ++k)
+        if (qlen <= t.q[k])
+            return k;
+    return t.n;
+}
+
+__global__ void pair_class_hist_kernel(const int64_t *__restrict__ q_off, int64_t n, const ClassTable t,
+                                       int32_t *hist)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[pair_class(q_off[i + 1] - q_off[i], t)], 1);
+}
+
+__global__ void pair_class_scan_kernel(const int32_t *hist, int32_t *cursor, int ncls)
+{
+    if (threadIdx.x == 0) {
+        int32_t s = 0;
+        for (int k = 0; k <= ncls; ++k) {
+            cursor[k] = s;
+            s += hist[k];
+        }
+    }
+}
+
+__global__ void pair_class_scatter_kernel(const int64_t *__restrict__ q_off, int64_t n, const ClassTable t,
+                                          int32_t *cursor, int32_t *__restrict__ order)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int pos = atomicAdd(&cursor[pair_class(q_off[i + 1] - q_off[i], t)], 1);
+        order[pos] = (int32_t)i;
+    }
+}
+
+int launch_pair_classes(const int64_t *q_off, int64_t n_pairs, const ClassTable &t, int32_t *hist, int32_t *cursor,
+                        int32_t *order, cudaStream_t st, int num_sms)
+{
+    if (n_pairs <= 0)
+        return (int)cudaSuccess;
+    int64_t blocks = (n_pairs + 255) / 256;
+    if (blocks > (int64_t)num_sms * 8)
+        blocks = (int64_t)num_sms * 8;
+    pair_class_hist_kernel<<<(unsigned)blocks, 256, 0, st>>>(q_off, n_pairs, t, hist);
+    pair_class_scan_kernel<<<1, 32, 0, st>>>(hist, cursor, t.n);
+    pair_class_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(q_off, n_pairs, t, cursor, order);
+    return (int)cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Integer-throughput probe.  Each thread updates K independent cells with the
 // exact per-cell instruction sequence of the batch kernel's plain pass (no

@@ -71,7 +71,7 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
 
     const T negO = LT::splat(-o);
     const T negE = LT::splat(-e);
-    const T negOS1 = LT::splat(-o - (S - 1) * e);
+    const T negS1 = LT::splat(-(S - 1) * e);
 
     T Ho[S], E[S];
 #pragma unroll
@@ -163,7 +163,9 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                 if (gl == 0)
                     cin = LT::zero();
                 c_prev = cin;
-                hlast = LT::max2(Ho[S - 1], LT::add(cin, negOS1));
+                // two adds: each constant stays inside the lane range, so a
+                // saturating lane floors at -128 instead of wrapping
+                hlast = LT::max2(Ho[S - 1], LT::add(LT::add(cin, negO), negS1));
                 if (has_next && gl == L - 1) {
 #pragma unroll
                     for (int c = 0; c < CELLS; ++c)

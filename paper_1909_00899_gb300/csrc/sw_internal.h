@@ -47,10 +47,26 @@ struct PairArgs {
     uint32_t *counter;
 };
 
-// batch launchers (sw_kernels_*.cu).  Return a cudaError_t.
-int launch_batch(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
-bool plan_supported(const Plan &pl, bool lazy);
-int launch_pairs(int lane, int qmax, const PairArgs &a, int num_sms, cudaStream_t st);
+// batch launchers (sw_k_i32.cu, sw_k_i16.cu, sw_k_i8.cu), declared in
+// sw_api.cu; every launcher returns a cudaError_t value.
+// pair launchers (sw_k_pairs.cu): one query-length class (L, S) per launch
+// over list[0 .. n_hint), or list[0 .. *count_dev) when count_dev is set
+// (*count_dev <= n_hint).
+int launch_pairs(int lane, int L, int S, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
+                 int64_t n_hint, int num_sms, cudaStream_t st);
+
+// Query-length classes of the pair kernel: class k holds pairs with
+// qlen <= q[k] (and > q[k-1]); class n holds longer queries.
+struct ClassTable {
+    int n;
+    int q[8];
+};
+// hist[n + 1] and cursor[n + 1] zeroed; order grouped by class, ascending.
+int launch_pair_classes(const int64_t *q_off, int64_t n_pairs, const ClassTable &t, int32_t *hist,
+                        int32_t *cursor, int32_t *order, cudaStream_t st, int num_sms);
+// flag list entries whose score reached thresh into out (count in *out_count)
+int launch_flag_overflow_list(const int32_t *scores, const int32_t *list, int64_t n, int32_t thresh, int32_t *out,
+                              int32_t *out_count, cudaStream_t st, int num_sms);
 
 // aux kernels (sw_aux.cu)
 int launch_profile_build(const uint8_t *d_query, int32_t qlen, const int8_t *d_M, int32_t A, const Plan &pl,
@@ -63,8 +79,6 @@ int launch_length_order(const int64_t *off, int64_t n, int32_t *order, int32_t *
 // Sequences whose score reached thresh -> list (count in *count, zero at launch).
 int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32_t *list, int32_t *count,
                          cudaStream_t st, int num_sms);
-int launch_flag_overflow_pairs(const int32_t *scores, const int64_t *q_off, int64_t n, int32_t thresh_base,
-                               int32_t *list, int32_t *count, cudaStream_t st, int num_sms);
 
 // Integer-op throughput probe for the ALU roofline: 'op' selects the
 // instruction stream; returns ops executed (lane-ops) and elapsed ms.

@@ -1,0 +1,37 @@
+// Pair-kernel instantiations: query-length classes per lane type.
+#include <algorithm>
+
+#include "sw_pairs.cuh"
+
+namespace swg {
+
+int launch_pairs(int lane, int L, int S, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
+                 int64_t n_hint, int num_sms, cudaStream_t st)
+{
+#define SWG_CASE(LT, LL, SS)                                                        \
+    if (L == LL && S == SS)                                                         \
+        return launch_pairs_inst<LT, LL, SS>(a, list, count_dev, n_hint, num_sms, st);
+    if (lane == LK_I32) {
+        SWG_CASE(LaneI32, 4, 8)
+        SWG_CASE(LaneI32, 8, 8)
+        SWG_CASE(LaneI32, 16, 8)
+        SWG_CASE(LaneI32, 16, 10)
+        SWG_CASE(LaneI32, 32, 8)
+        SWG_CASE(LaneI32, 32, 16)
+    } else if (lane == LK_I16X2) {
+        SWG_CASE(LaneI16x2, 8, 8)
+        SWG_CASE(LaneI16x2, 16, 8)
+        SWG_CASE(LaneI16x2, 16, 10)
+        SWG_CASE(LaneI16x2, 32, 8)
+        SWG_CASE(LaneI16x2, 32, 16)
+    } else if (lane == LK_I8X4) {
+        SWG_CASE(LaneI8x4, 8, 16)
+        SWG_CASE(LaneI8x4, 16, 10)
+        SWG_CASE(LaneI8x4, 16, 16)
+        SWG_CASE(LaneI8x4, 32, 16)
+    }
+#undef SWG_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace swg

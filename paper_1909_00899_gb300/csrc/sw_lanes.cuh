@@ -63,7 +63,12 @@ struct LaneI16x2 {
     static constexpr int PAD = -16384;
     static constexpr int CEIL = 32767;
 
-    __device__ __forceinline__ static T splat(int v) { return (uint32_t)(v & 0xffff) * 0x10001u; }
+    // constants saturate to the lane range
+    __device__ __forceinline__ static T splat(int v)
+    {
+        v = max(-32768, min(32767, v));
+        return (uint32_t)(v & 0xffff) * 0x10001u;
+    }
     __device__ __forceinline__ static T zero() { return 0u; }
     __device__ __forceinline__ static T addmax_relu(T a, T b, T c) { return __viaddmax_s16x2_relu(a, b, c); }
     __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s16x2(a, b, c); }
@@ -111,7 +116,14 @@ struct LaneI8x4 {
     static constexpr int PAD = -128;
     static constexpr int CEIL = 127;
 
-    __device__ __forceinline__ static T splat(int v) { return (uint32_t)(v & 0xff) * 0x01010101u; }
+    // constants saturate to the lane range: a clamped negative weight gives
+    // a saturated sum <= max(true sum, -128), which is inert wherever the
+    // true sum was (every kept value is >= -o >= -127)
+    __device__ __forceinline__ static T splat(int v)
+    {
+        v = max(-128, min(127, v));
+        return (uint32_t)(v & 0xff) * 0x01010101u;
+    }
     __device__ __forceinline__ static T zero() { return 0u; }
     // saturating byte adds: a sum above 127 pins at 127 and flags the alignment
     __device__ __forceinline__ static T addmax_relu(T a, T b, T c)

@@ -13,7 +13,7 @@ namespace swg {
 
 template <class LT, int L, int S>
 __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const int32_t *__restrict__ list,
-                                                       const int32_t *__restrict__ count_dev)
+                                                       const int32_t *__restrict__ count_dev, int64_t n_list)
 {
     using T = typename LT::T;
     using Elem = typename LT::Elem;
@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
     for (int c = 0; c < CELLS; ++c)
         pbase[c] = gprof + c * cell_elems;
 
-    const int64_t n_work = count_dev ? (int64_t)(*count_dev) : p.n_pairs;
+    // entries of list to process: the class size, or a count on the device
+    const int64_t n_work = count_dev ? (int64_t)(*count_dev) : n_list;
     const int64_t units = (n_work + CELLS - 1) / CELLS;
     unsigned long long unused = 0;
 
@@ -140,7 +141,7 @@ int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *cou
         grid = need;
     if (grid < 1)
         return (int)cudaSuccess;
-    kern<<<(unsigned)grid, warps * 32, smem, st>>>(a, list, count_dev);
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(a, list, count_dev, n_hint);
     return (int)cudaGetLastError();
 }
 

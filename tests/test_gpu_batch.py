@@ -178,3 +178,73 @@ def test_cell_rate_probe_runs(sw):
     for lane in (sw.SW_LANE_I32, sw.SW_LANE_I16X2, sw.SW_LANE_I8X4):
         r = sw.sw_probe_cell_rate(lane, 256)
         assert r > 1e9
+
+
+# ---------------------------------------------------------------------------
+# sw_align_pairs: each pair with its own query
+# ---------------------------------------------------------------------------
+
+PAIR_LANES = ["i32", "i16x2", "i8x4", "auto"]
+
+
+def run_pairs(sw, kind, q, q_off, r, r_off, M, o, e):
+    lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i8x4": sw.SW_LANE_I8X4,
+            "auto": sw.SW_LANE_AUTO}[kind]
+    qd, qo = db_to_dev(q, q_off)
+    rd, ro = db_to_dev(r, r_off)
+    n = len(q_off) - 1
+    out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    sw.sw_align_pairs(qd, qo, rd, ro, M, o, e, out, lane_type=lane)
+    torch.cuda.synchronize()
+    return out[:n].cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", PAIR_LANES)
+def test_pairs_reads_vs_windows(sw, kind):
+    """DNA reads (95%/99% copies, 40-200 bp indels) against their own 2 kbp
+    windows, match +1 mismatch -4, o=6 e=1."""
+    w = synth.workload_reads(n_pairs=1500)
+    want = oracle.gotoh_pairs(w["q"], w["q_off"], w["r"], w["r_off"], w["M"], w["o"], w["e"])
+    got = run_pairs(sw, kind, w["q"], w["q_off"], w["r"], w["r_off"], w["M"], w["o"], w["e"])
+    np.testing.assert_array_equal(got, want)
+    assert want.max() > 127  # the 8-bit lanes must have overflowed and been rescored
+
+
+@pytest.mark.parametrize("kind", PAIR_LANES)
+def test_pairs_mixed_query_lengths(sw, kind):
+    """Query lengths 0..512 across every class, ragged references (some
+    empty), protein scoring."""
+    rng = np.random.default_rng(1101)
+    M = synth.protein_matrix(rng)
+    qlens = np.concatenate([[0, 1, 2, 512, 511, 160, 161, 128, 129, 256, 257],
+                            rng.integers(0, 513, 300)]).astype(np.int64)
+    rlens = rng.integers(0, 700, len(qlens)).astype(np.int64)
+    rlens[:3] = 0
+    q, q_off = synth.pack(qlens, rng, 20)
+    r, r_off = synth.pack(rlens, rng, 20)
+    want = oracle.gotoh_pairs(q, q_off, r, r_off, M, 11, 1)
+    got = run_pairs(sw, kind, q, q_off, r, r_off, M, 11, 1)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_pairs_query_too_long(sw):
+    rng = np.random.default_rng(1102)
+    M = synth.dna_matrix()
+    q, q_off = synth.pack(np.array([100, 600], np.int64), rng, 4)
+    r, r_off = synth.pack(np.array([200, 200], np.int64), rng, 4)
+    with pytest.raises(sw.SwError) as ei:
+        run_pairs(sw, "auto", q, q_off, r, r_off, M, 6, 1)
+    assert ei.value.code == sw.SW_ERR_RANGE
+
+
+@pytest.mark.parametrize("kind", PAIR_LANES)
+def test_pairs_gap_adversary(sw, kind):
+    rng = np.random.default_rng(1103)
+    M = synth.dna_matrix()
+    queries, refs = gap_adversary(rng, 4, 400, xlo=20, xhi=120, ylo=40, yhi=200)
+    queries = [x[:512] for x in queries]
+    q, q_off = pack_list(queries)
+    r, r_off = pack_list(refs)
+    want = oracle.gotoh_pairs(q, q_off, r, r_off, M, 6, 1)
+    got = run_pairs(sw, kind, q, q_off, r, r_off, M, 6, 1)
+    np.testing.assert_array_equal(got, want)
