@@ -69,16 +69,39 @@ typedef struct sw_profile sw_profile; /* opaque, owned by the library */
  *                 length, query chunks) is chosen from qlen and lane_type
  *   cuda_stream   stream for the upload and the profile-build kernel
  *   out           receives the profile; free with sw_profile_free
- * Device memory for the profile is allocated here (synchronously) on the
- * current device.  Errors: SW_ERR_INVALID (qlen < 0, alphabet out of range,
- * null pointers), SW_ERR_NOMEM, SW_ERR_CUDA.
+ * Device memory for the profile is one stream-ordered allocation
+ * (cudaMallocAsync on cuda_stream, current device); work on other streams
+ * that uses the profile must be ordered after the build (an event, or a
+ * synchronisation).  The host buffers are read before the call returns.
+ * Errors: SW_ERR_INVALID (qlen < 0, alphabet out of range, null pointers,
+ * query code >= alphabet), SW_ERR_NOMEM, SW_ERR_CUDA.
  */
 int sw_profile_build(const uint8_t *query, int32_t qlen,
                      const int8_t *subst_matrix, int32_t alphabet,
                      int32_t lane_type, void *cuda_stream, sw_profile **out);
 
-/* Releases a profile (waits for the device to finish with it).  NULL ok. */
+/*
+ * sw_profile_build_ex — as sw_profile_build with an explicit layout: lanes
+ * per alignment (the paper's p, a power of two up to 32) and seg_len query
+ * positions per lane (segLen); both 0 selects the built-in table.  Only the
+ * shapes the kernels are compiled for are accepted (SW_ERR_INVALID
+ * otherwise): int32 {4x8, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16},
+ * s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16}, s8x4 {8x16, 16x16,
+ * 32x16}.  Used by the autotuner.
+ */
+int sw_profile_build_ex(const uint8_t *query, int32_t qlen,
+                        const int8_t *subst_matrix, int32_t alphabet,
+                        int32_t lane_type, int32_t lanes, int32_t seg_len,
+                        void *cuda_stream, sw_profile **out);
+
+/* Releases a profile after waiting for the whole device to finish (safe
+ * whatever stream used it).  NULL ok. */
 int sw_profile_free(sw_profile *prof);
+
+/* Releases a profile in stream order on cuda_stream, without waiting: every
+ * use of the profile must already be ordered before this point of that
+ * stream.  The handle is invalid on return.  NULL ok. */
+int sw_profile_free_async(sw_profile *prof, void *cuda_stream);
 
 /* Describes a profile's plan: lanes per alignment, segment length per lane,
  * query chunks, lane type actually used.  Any out pointer may be NULL. */
@@ -116,6 +139,26 @@ int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues,
                          const int64_t *db_offsets, int64_t n_db,
                          int32_t gap_open, int32_t gap_extend,
                          int32_t *scores_out, void *cuda_stream);
+
+/*
+ * sw_db — a database kept resident on the device: the caller's residue and
+ * offset buffers (which must outlive the handle) plus, computed once by
+ * sw_db_create, the length-binned processing order (longest first) and the
+ * total residue count.  sw_db_create synchronises cuda_stream once;
+ * sw_align_db / sw_align_lazyf_db then read nothing back and allocate their
+ * scratch with cudaMallocAsync on the call's stream, so they can be captured
+ * into a CUDA graph, and calls on different streams may overlap.
+ * Errors as sw_align_batch; sw_db_free releases the handle (NULL ok).
+ */
+typedef struct sw_db sw_db; /* opaque, owned by the library */
+int sw_db_create(const uint8_t *db_residues, const int64_t *db_offsets,
+                 int64_t n_db, void *cuda_stream, sw_db **out);
+int sw_db_free(sw_db *db);
+int sw_align_db(const sw_profile *prof, const sw_db *db, int32_t gap_open,
+                int32_t gap_extend, int32_t *scores_out, void *cuda_stream);
+int sw_align_lazyf_db(const sw_profile *prof, const sw_db *db,
+                      int32_t gap_open, int32_t gap_extend,
+                      int32_t *scores_out, void *cuda_stream);
 
 /*
  * sw_align_pairs — n_pairs independent alignments, pair k aligning query

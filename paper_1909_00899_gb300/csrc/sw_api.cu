@@ -28,11 +28,22 @@ struct sw_profile {
     int32_t qlen = 0, A = 0, lane = 0;
     Plan plan;    // plan of the requested lane type
     Plan plan32;  // int32 plan: lazy-F and the rescore of flagged alignments
+    void *block = nullptr;        // one stream-ordered allocation for all parts
+    cudaStream_t stream = nullptr;  // stream the profile was built on
     uint8_t *d_query = nullptr;
     int8_t *d_M = nullptr;
     int8_t *d_prof = nullptr;
     int8_t *d_prof32 = nullptr;
     int32_t maxM = 0, minM = 0;
+};
+
+struct sw_db {
+    int device = 0;
+    const uint8_t *res = nullptr;
+    const int64_t *off = nullptr;
+    int64_t n = 0;
+    int64_t total = 0;
+    int32_t *order = nullptr;  // length-binned order, longest first (owned)
 };
 
 namespace {
@@ -97,6 +108,21 @@ struct Choice {
 const Choice kI32[] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {32, 16}};
 const Choice kI16[] = {{8, 8}, {16, 8}, {32, 8}, {32, 16}};
 const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
+// every (lanes, segment length) the batch kernels are instantiated for
+const Choice kAllI32[] = {{4, 8}, {8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}};
+const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}};
+const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
+
+bool plan_supported(int lane, int L, int S)
+{
+    const Choice *t = lane == SW_LANE_I32 ? kAllI32 : (lane == SW_LANE_I16X2 ? kAllI16 : kAllI8);
+    const int n = lane == SW_LANE_I32 ? 8 : (lane == SW_LANE_I16X2 ? 7 : 3);
+    for (int i = 0; i < n; ++i)
+        if (t[i].L == L && t[i].S == S)
+            return true;
+    return false;
+}
+
 // query-length classes of the pair kernel (one query per pair, <= 512)
 const Choice kPairI32[] = {{4, 8}, {8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
 const Choice kPairI16[] = {{8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
@@ -132,13 +158,16 @@ bool lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan 
     if (lane == SW_LANE_I32)
         return true;
     const int64_t ceil = lane == SW_LANE_I16X2 ? 32767 : 127;
-    if ((int64_t)pf->maxM + o > ceil)
+    if (lane == SW_LANE_I8X4 && (int64_t)pf->maxM + o > ceil)
         return false;
-    if (o > ceil)
+    if (o > 127)
         return false;
     if (lane == SW_LANE_I16X2) {
-        // scan hop weights and decays stay far from the wrap point
-        if ((int64_t)o + (int64_t)pl.L * pl.S * e + 256 > 16000)
+        // biased halves stay positive: 2o + S*e below the X-space bias (4096),
+        // the deepest scan hop above -32768
+        if (2LL * o + (int64_t)pl.S * e + 256 > 4096)
+            return false;
+        if (4096LL - o - (int64_t)(pl.L / 2) * pl.S * e < -32000)
             return false;
     } else {
         // the last-position correction subtracts (S-1)*e in one saturating add
@@ -146,6 +175,18 @@ bool lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan 
             return false;
     }
     return true;
+}
+
+// True score from which a packed lane's result is rescored in int32: the
+// first addition H + M that can leave the lane range needs H above it.
+int32_t flag_threshold(int lane, int32_t o, int32_t maxM)
+{
+    const int32_t m = std::max(maxM, 0);
+    if (lane == SW_LANE_I16X2)
+        return 32767 - (4096 + 128 - o) - m;  // s16x2: h-space bias 4096 + 128 - o
+    if (lane == SW_LANE_I8X4)
+        return 127 - m;
+    return INT32_MAX;
 }
 
 struct Scratch {
@@ -191,8 +232,11 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
     return swg::launch_batch_i8(pl, a, sms, st);
 }
 
+// pre_order / pre_total: a database handle's persistent length order and
+// residue count (then no order kernels run and nothing is read back).
 int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o, int32_t e,
-               int32_t *scores, void *stream, bool lazy)
+               int32_t *scores, void *stream, bool lazy, const int32_t *pre_order = nullptr,
+               int64_t pre_total = -1)
 {
     int rc = check_align_args(prof, db, off, n_db, o, e, scores);
     if (rc)
@@ -220,9 +264,9 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     const int C32 = prof->plan32.C;
 
     // total residues, needed only to size the boundary rows of long queries
-    int64_t total = 0;
+    int64_t total = pre_total > 0 ? pre_total : 0;
     const bool chunked = main.C > 1 || (packed && C32 > 1);
-    if (chunked) {
+    if (chunked && pre_total < 0) {
         cudaError_t err = cudaMemcpyAsync(&total, off + n_db, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess)
             err = cudaStreamSynchronize(st);
@@ -234,7 +278,7 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
 
     const size_t n = (size_t)n_db;
     const int ncount = main.C + (packed ? C32 : 0) + 2;
-    const size_t sz_order = align_up(n * 4);
+    const size_t sz_order = pre_order ? 0 : align_up(n * 4);
     const size_t sz_zero = align_up((2 * swg::NBINS + ncount) * 4);
     const size_t sz_list = packed ? align_up(n * 4) : 0;
     const size_t sz_bnd = chunked ? align_up((size_t)total * sizeof(int2) + 16) : 0;
@@ -246,7 +290,7 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
         return cuda_fail(err, "cudaMallocAsync(scratch)");
     }
     char *p = (char *)sc.base;
-    int32_t *order = (int32_t *)p;
+    int32_t *order = pre_order ? const_cast<int32_t *>(pre_order) : (int32_t *)p;
     int32_t *zero = (int32_t *)(p + sz_order);
     int32_t *bins = zero;
     uint32_t *counters = (uint32_t *)(zero + 2 * swg::NBINS);
@@ -257,9 +301,12 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     err = cudaMemsetAsync(zero, 0, sz_zero, st);
     if (err != cudaSuccess)
         return cuda_fail(err, "cudaMemsetAsync(scratch)");
-    int kr = swg::launch_length_order(off, n_db, order, bins, st, sms);
-    if (kr)
-        return cuda_fail(kr, "length order kernels");
+    int kr = 0;
+    if (!pre_order) {
+        kr = swg::launch_length_order(off, n_db, order, bins, st, sms);
+        if (kr)
+            return cuda_fail(kr, "length order kernels");
+    }
 
     swg::BatchArgs a;
     memset(&a, 0, sizeof(a));
@@ -273,6 +320,8 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     a.e = e;
     a.bnd = bnd;
     a.scores = scores;
+    a.one = 1;
+    a.flag_thresh = flag_threshold(lane, o, prof->maxM);
     a.prof = main_prof;
     a.nchunks = main.C;
     for (int c = 0; c < main.C; ++c) {
@@ -283,11 +332,11 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
             return cuda_fail(kr, "batch kernel launch");
     }
     if (packed) {
-        const int32_t thresh = (lane == SW_LANE_I16X2 ? 32767 : 127) - std::max(prof->maxM, 0);
-        kr = swg::launch_flag_overflow(scores, n_db, thresh, list, list_count, st, sms);
+        kr = swg::launch_flag_overflow(scores, n_db, a.flag_thresh, list, list_count, st, sms);
         if (kr)
             return cuda_fail(kr, "overflow flag kernel");
         a.prof = prof->d_prof32;
+        a.flag_thresh = INT32_MAX;
         a.nchunks = C32;
         a.order = list;
         a.n_work = n_db;
@@ -313,6 +362,12 @@ const char *sw_version(void) { return "0.1.0"; }
 
 int sw_profile_build(const uint8_t *query, int32_t qlen, const int8_t *subst_matrix, int32_t alphabet,
                      int32_t lane_type, void *cuda_stream, sw_profile **out)
+{
+    return sw_profile_build_ex(query, qlen, subst_matrix, alphabet, lane_type, 0, 0, cuda_stream, out);
+}
+
+int sw_profile_build_ex(const uint8_t *query, int32_t qlen, const int8_t *subst_matrix, int32_t alphabet,
+                        int32_t lane_type, int32_t lanes, int32_t seg_len, void *cuda_stream, sw_profile **out)
 {
     if (!out)
         return fail(SW_ERR_INVALID, "out is NULL");
@@ -341,37 +396,48 @@ int sw_profile_build(const uint8_t *query, int32_t qlen, const int8_t *subst_mat
         pf->minM = std::min<int32_t>(pf->minM, subst_matrix[i]);
     }
     int lane = lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type;
+    if ((lanes == 0) != (seg_len == 0) || (lanes && !plan_supported(lane, lanes, seg_len))) {
+        delete pf;
+        return fail(SW_ERR_INVALID, "no kernel for lane type %d with %d lanes x %d positions", lane, lanes, seg_len);
+    }
     pf->lane = lane;
     pf->plan = choose_plan(qlen, lane);
-    pf->plan32 = choose_plan(qlen, SW_LANE_I32);
+    if (lanes) {
+        pf->plan.L = lanes;
+        pf->plan.S = seg_len;
+        pf->plan.C = qlen > 0 ? (qlen + lanes * seg_len - 1) / (lanes * seg_len) : 0;
+    }
+    // int32 profiles serve lazy-F and the rescore with their own layout
+    pf->plan32 = lane == SW_LANE_I32 ? pf->plan : choose_plan(qlen, SW_LANE_I32);
     cudaGetDevice(&pf->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    pf->stream = st;
+    keep_pool_warm(pf->device);
 
+    const size_t qbytes = align_up((size_t)std::max(qlen, 1));
+    const size_t mbytes = align_up((size_t)alphabet * alphabet);
+    const size_t pbytes = align_up((size_t)pf->plan.C * alphabet * pf->plan.L * pf->plan.S);
+    const size_t p32bytes =
+        lane == SW_LANE_I32 ? 0 : align_up((size_t)pf->plan32.C * alphabet * pf->plan32.L * pf->plan32.S);
+    cudaError_t err = cudaMallocAsync(&pf->block, qbytes + mbytes + pbytes + p32bytes, st);
+    if (err != cudaSuccess) {
+        pf->block = nullptr;
+        delete pf;
+        return cuda_fail(err, "cudaMallocAsync(profile)");
+    }
+    char *base = (char *)pf->block;
+    pf->d_query = (uint8_t *)base;
+    pf->d_M = (int8_t *)(base + qbytes);
+    pf->d_prof = (int8_t *)(base + qbytes + mbytes);
+    pf->d_prof32 = lane == SW_LANE_I32 ? pf->d_prof : (int8_t *)(base + qbytes + mbytes + pbytes);
     auto cleanup = [&](int code) {
-        sw_profile_free(pf);
+        sw_profile_free_async(pf, st);
         return code;
     };
-    const size_t qbytes = (size_t)std::max(qlen, 1);
-    const size_t mbytes = (size_t)alphabet * alphabet;
-    const size_t pbytes = (size_t)pf->plan.C * alphabet * pf->plan.L * pf->plan.S;
-    const size_t p32bytes = (size_t)pf->plan32.C * alphabet * pf->plan32.L * pf->plan32.S;
-    cudaError_t err = cudaMalloc(&pf->d_query, qbytes);
-    if (err == cudaSuccess)
-        err = cudaMalloc(&pf->d_M, mbytes);
-    if (err == cudaSuccess && pbytes)
-        err = cudaMalloc(&pf->d_prof, pbytes);
-    if (err == cudaSuccess && p32bytes) {
-        if (lane == SW_LANE_I32)
-            pf->d_prof32 = pf->d_prof;
-        else
-            err = cudaMalloc(&pf->d_prof32, p32bytes);
-    }
-    if (err != cudaSuccess)
-        return cleanup(cuda_fail(err, "cudaMalloc(profile)"));
     if (qlen > 0)
         err = cudaMemcpyAsync(pf->d_query, query, (size_t)qlen, cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(pf->d_M, subst_matrix, mbytes, cudaMemcpyHostToDevice, st);
+        err = cudaMemcpyAsync(pf->d_M, subst_matrix, (size_t)alphabet * alphabet, cudaMemcpyHostToDevice, st);
     if (err != cudaSuccess)
         return cleanup(cuda_fail(err, "profile upload"));
     if (qlen > 0) {
@@ -389,16 +455,24 @@ int sw_profile_free(sw_profile *prof)
 {
     if (!prof)
         return SW_OK;
-    if (prof->d_prof32 && prof->d_prof32 != prof->d_prof)
-        cudaFree(prof->d_prof32);
-    if (prof->d_prof)
-        cudaFree(prof->d_prof);
-    if (prof->d_M)
-        cudaFree(prof->d_M);
-    if (prof->d_query)
-        cudaFree(prof->d_query);
+    // the profile may be in use on any stream: wait for the device first
+    cudaError_t err = cudaDeviceSynchronize();
+    if (prof->block)
+        cudaFreeAsync(prof->block, prof->stream);
+    cudaStreamSynchronize(prof->stream);
     delete prof;
-    return SW_OK;
+    return err == cudaSuccess ? SW_OK : cuda_fail(err, "sw_profile_free");
+}
+
+int sw_profile_free_async(sw_profile *prof, void *cuda_stream)
+{
+    if (!prof)
+        return SW_OK;
+    cudaError_t err = cudaSuccess;
+    if (prof->block)
+        err = cudaFreeAsync(prof->block, (cudaStream_t)cuda_stream);
+    delete prof;
+    return err == cudaSuccess ? SW_OK : cuda_fail(err, "cudaFreeAsync(profile)");
 }
 
 int sw_profile_plan(const sw_profile *prof, int32_t *lanes, int32_t *seg_len, int32_t *chunks, int32_t *lane_type)
@@ -427,6 +501,84 @@ int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues, con
                          void *cuda_stream)
 {
     return align_impl(prof, db_residues, db_offsets, n_db, gap_open, gap_extend, scores_out, cuda_stream, true);
+}
+
+int sw_db_create(const uint8_t *db_residues, const int64_t *db_offsets, int64_t n_db, void *cuda_stream,
+                 sw_db **out)
+{
+    if (!out)
+        return fail(SW_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n_db < 0 || n_db > INT32_MAX - 1024)
+        return fail(SW_ERR_INVALID, "n_db out of range (%lld)", (long long)n_db);
+    if (n_db > 0 && (!db_residues || !db_offsets))
+        return fail(SW_ERR_INVALID, "null device pointer");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    sw_db *d = new sw_db();
+    cudaGetDevice(&d->device);
+    d->res = db_residues;
+    d->off = db_offsets;
+    d->n = n_db;
+    if (n_db == 0) {
+        *out = d;
+        return SW_OK;
+    }
+    int32_t *bins = nullptr;
+    cudaError_t err = cudaMalloc(&d->order, sizeof(int32_t) * (size_t)n_db);
+    if (err == cudaSuccess)
+        err = cudaMalloc(&bins, sizeof(int32_t) * 2 * swg::NBINS);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(bins, 0, sizeof(int32_t) * 2 * swg::NBINS, st);
+    if (err != cudaSuccess) {
+        if (bins)
+            cudaFree(bins);
+        sw_db_free(d);
+        return cuda_fail(err, "sw_db_create allocation");
+    }
+    int kr = swg::launch_length_order(db_offsets, n_db, d->order, bins, st, num_sms_of(d->device));
+    if (!kr)
+        kr = (int)cudaMemcpyAsync(&d->total, db_offsets + n_db, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (!kr)
+        kr = (int)cudaStreamSynchronize(st);
+    cudaFree(bins);
+    if (kr) {
+        sw_db_free(d);
+        return cuda_fail(kr, "sw_db_create");
+    }
+    if (d->total < 0) {
+        sw_db_free(d);
+        return fail(SW_ERR_INVALID, "db_offsets[n_db] < 0");
+    }
+    *out = d;
+    return SW_OK;
+}
+
+int sw_db_free(sw_db *db)
+{
+    if (!db)
+        return SW_OK;
+    if (db->order)
+        cudaFree(db->order);
+    delete db;
+    return SW_OK;
+}
+
+int sw_align_db(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32_t gap_extend, int32_t *scores_out,
+                void *cuda_stream)
+{
+    if (!db)
+        return fail(SW_ERR_INVALID, "db is NULL");
+    return align_impl(prof, db->res, db->off, db->n, gap_open, gap_extend, scores_out, cuda_stream, false,
+                      db->order, db->total);
+}
+
+int sw_align_lazyf_db(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32_t gap_extend,
+                      int32_t *scores_out, void *cuda_stream)
+{
+    if (!db)
+        return fail(SW_ERR_INVALID, "db is NULL");
+    return align_impl(prof, db->res, db->off, db->n, gap_open, gap_extend, scores_out, cuda_stream, true,
+                      db->order, db->total);
 }
 
 int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
@@ -539,7 +691,8 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
     a.o = gap_open;
     a.e = gap_extend;
     a.scores = scores_out;
-    const int32_t thresh = (lane == SW_LANE_I16X2 ? 32767 : 127) - std::max(maxM, 0);
+    a.one = 1;
+    const int32_t thresh = flag_threshold(lane, gap_open, maxM);
     int64_t begin = 0;
     for (int k = 0; k < ncls; ++k) {
         const int64_t cnt = h_hist[k];
@@ -548,6 +701,7 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
         const int32_t *cls = order + begin;
         a.counter = counters + 2 * k;
         const int lk = lane == SW_LANE_I32 ? swg::LK_I32 : (lane == SW_LANE_I16X2 ? swg::LK_I16X2 : swg::LK_I8X4);
+        a.flag_thresh = thresh;
         kr = swg::launch_pairs(lk, tab[k].L, tab[k].S, a, cls, nullptr, cnt, sms, st);
         if (kr)
             return cuda_fail(kr, "pair kernel launch");
@@ -561,6 +715,7 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
             while (j + 1 < kPairI32N && kPairI32[j].L * kPairI32[j].S < ct.q[k])
                 ++j;
             a.counter = counters + 2 * k + 1;
+            a.flag_thresh = INT32_MAX;
             kr = swg::launch_pairs(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, a, cl, list_count + k, cnt, sms, st);
             if (kr)
                 return cuda_fail(kr, "rescore kernel launch");
@@ -599,14 +754,13 @@ int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_secon
     int dev = 0;
     cudaGetDevice(&dev);
     const int sms = num_sms_of(dev);
-    double lane_ops = 0;
+    double cells = 0;
     float ms = 0;
     const int op = lane_type - 1;
-    int kr = swg::run_int_peak(op, sms * 8, 256, iters, &lane_ops, &ms, (cudaStream_t)cuda_stream);
+    int kr = swg::run_int_peak(op, sms * 8, 256, iters, &cells, &ms, (cudaStream_t)cuda_stream);
     if (kr)
         return cuda_fail(kr, "cell-rate probe");
-    const double cells_per_op = lane_type == SW_LANE_I32 ? 1.0 : (lane_type == SW_LANE_I16X2 ? 2.0 : 4.0);
-    *cells_per_second = ms > 0 ? lane_ops / 6.0 * cells_per_op / (ms * 1e-3) : 0.0;
+    *cells_per_second = ms > 0 ? cells / (ms * 1e-3) : 0.0;
     return SW_OK;
 }
 

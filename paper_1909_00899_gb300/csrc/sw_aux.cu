@@ -201,37 +201,41 @@ int launch_pair_classes(const int64_t *q_off, int64_t n_pairs, const ClassTable 
 }
 
 // ---------------------------------------------------------------------------
-// Integer-throughput probe.  Each thread updates K independent cells with the
-// exact per-cell instruction sequence of the batch kernel's plain pass (no
-// loads, no shuffles), so the measured rate is the ALU ceiling of the cell
-// update for that lane type.  op 0: int32 cells, 1: s16x2, 2: s8x4.
+// Cell-rate probe.  Each thread updates K positions per column with the
+// exact instruction sequence of the plain scan-F pass (no loads, shuffles,
+// scan or correction), so the measured rate is the ceiling of that sequence
+// on this GPU.  op 0: int32 cells, 1: s16x2, 2: s8x4.
 // ---------------------------------------------------------------------------
 template <class LT>
-__global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, int *sink)
+__global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uint32_t one, int *sink)
 {
     using T = typename LT::T;
     constexpr int K = 16;
-    T Ho[K], E[K];
-    const T negO = LT::splat(-11), negE = LT::splat(-1);
-    T P0 = LT::splat((seed + threadIdx.x) & 7), P1 = LT::splat(((seed >> 3) + threadIdx.x) & 7);
+    const typename LT::K k = LT::consts(11, 1, K, one);
+    T X[K], E[K];
+    T P0 = LT::splat(((seed + threadIdx.x) & 7) + 11), P1 = LT::splat((((seed >> 3) + threadIdx.x) & 7) + 11);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        Ho[j] = LT::splat((j + threadIdx.x) & 15);
-        E[j] = LT::zero();
+        X[j] = k.xinit;
+        E[j] = k.hzero;
     }
-    T mx = LT::zero();
+    T mx = k.hzero;
     for (int it = 0; it < iters; ++it) {
-        T hd = Ho[K - 1];
-        T F = LT::zero();
+        T hd = X[K - 1];
+        T F = k.xzero;
+        T hpair = k.hzero;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const T h = LT::addmax_relu(hd, (j & 1) ? P1 : P0, E[j]);
-            hd = Ho[j];
-            const T ho = LT::add(h, negO);
-            Ho[j] = LT::addmax(F, negO, ho);
-            E[j] = LT::addmax(E[j], negE, Ho[j]);
-            F = LT::addmax(F, negE, ho);
-            mx = LT::max2(mx, h);
+            const T h = LT::h_of(hd, (j & 1) ? P1 : P0, E[j], k);
+            hd = X[j];
+            const T ho = LT::ho_of(h, k);
+            X[j] = LT::addmax(F, k.negO, ho);
+            E[j] = LT::e_next(E[j], X[j], k);
+            F = LT::addmax(F, k.negE, ho);
+            if (j & 1)
+                mx = LT::max3(mx, hpair, h);
+            else
+                hpair = h;
         }
         const T t = P0;
         P0 = P1;
@@ -240,13 +244,13 @@ __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, int
     int acc = 0;
 #pragma unroll
     for (int j = 0; j < K; ++j)
-        acc ^= (int)Ho[j] ^ (int)E[j];
+        acc ^= (int)X[j] ^ (int)E[j];
     acc ^= (int)mx;
     if (acc == 0x7fffffff)
         sink[0] = acc;
 }
 
-int run_int_peak(int op, int blocks, int threads, int iters, double *lane_ops, float *ms, cudaStream_t st)
+int run_int_peak(int op, int blocks, int threads, int iters, double *cells, float *ms, cudaStream_t st)
 {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -255,13 +259,14 @@ int run_int_peak(int op, int blocks, int threads, int iters, double *lane_ops, f
     cudaError_t err = cudaMallocAsync((void **)&sink, sizeof(int), st);
     if (err != cudaSuccess)
         return (int)err;
+    const uint32_t one = 1;
     auto go = [&](void) {
         if (op == 0)
-            cell_peak_kernel<LaneI32><<<blocks, threads, 0, st>>>(iters, 12345, sink);
+            cell_peak_kernel<LaneI32><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
         else if (op == 1)
-            cell_peak_kernel<LaneI16x2><<<blocks, threads, 0, st>>>(iters, 12345, sink);
+            cell_peak_kernel<LaneI16x2><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
         else
-            cell_peak_kernel<LaneI8x4><<<blocks, threads, 0, st>>>(iters, 12345, sink);
+            cell_peak_kernel<LaneI8x4><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
     };
     go();  // warm-up
     cudaEventRecord(a, st);
@@ -276,8 +281,8 @@ int run_int_peak(int op, int blocks, int threads, int iters, double *lane_ops, f
     cudaEventDestroy(b);
     if (err != cudaSuccess)
         return (int)err;
-    // 6 instructions per cell-update (addmax_relu, add, 3 x addmax, max)
-    *lane_ops = 6.0 * 16.0 * (double)iters * (double)blocks * (double)threads;
+    const int cells_per_reg = op == 0 ? 1 : (op == 1 ? 2 : 4);
+    *cells = 16.0 * (double)iters * (double)blocks * (double)threads * cells_per_reg;
     *ms = t;
     return (int)cudaGetLastError();
 }

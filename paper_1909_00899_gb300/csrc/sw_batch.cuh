@@ -54,35 +54,37 @@ struct SegPad {
 };
 
 // One work unit (CELLS alignments, one query chunk) on a group of L lanes.
-// pbase[c]: staged profile of cell c (biased by +o); ref + start[c]: the
-// reference residues of cell c, len[c] of them; ncols: warp-uniform number
-// of columns to run (max over the warp).  Returns the group's packed
-// maximum of H.
+// pbase[c]: staged profile of cell c; ref + start[c]: the reference residues
+// of cell c, len[c] of them; ncols: warp-uniform number of columns to run
+// (max over the warp).  Returns the group's packed maximum of h (h-space).
 template <class LT, int L, int S, bool LAZY>
 __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *const *pbase, const uint8_t *ref,
                                                         const int64_t *start, const int *len, int ncols, int A,
-                                                        int o, int e, bool has_prev, bool has_next, int2 *bnd,
-                                                        int gl, unsigned long long &lazy_steps)
+                                                        int o, int e, uint32_t one, bool has_prev, bool has_next,
+                                                        int2 *bnd, int gl, unsigned long long &lazy_steps)
 {
     using T = typename LT::T;
     constexpr int CELLS = LT::CELLS;
     constexpr int SP = SegPad<S, LT::VEC>::value;
+    constexpr int LOGL = L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : L == 16 ? 4 : 5;
     constexpr unsigned FULL = 0xffffffffu;
 
-    const T negO = LT::splat(-o);
-    const T negE = LT::splat(-e);
-    const T negS1 = LT::splat(-(S - 1) * e);
+    const typename LT::K k = LT::consts(o, e, S, one);
+    T negW[LOGL];  // scan hop weights -(2^i)*S*e
+#pragma unroll
+    for (int i = 0; i < LOGL; ++i)
+        negW[i] = LT::splat(-(1 << i) * S * e);
 
-    T Ho[S], E[S];
+    T X[S], E[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-        Ho[j] = negO;
-        E[j] = LT::zero();
+        X[j] = k.xinit;
+        E[j] = k.hzero;
     }
-    T c_prev = LT::zero();  // carry into this lane from the previous column
-    T hlast = negO;         // corrected H - o of the last position, previous column
-    T hb_prev = negO;       // previous chunk's last H - o at the previous column
-    T mx = LT::zero();
+    T c_prev = k.xzero;   // carry into this lane from the previous column
+    T hlast = k.xinit;    // corrected X of the last position, previous column
+    T hb_prev = k.xinit;  // previous chunk's last X at the previous column
+    T mx = k.hzero;
 
     for (int r0 = 0; r0 < ncols; r0 += L) {
         int myres[CELLS];
@@ -106,8 +108,8 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
             T P[S];
             LT::template load_profile<L, S, SP>(pbase, res, gl, P);
 
-            T hd = LT::shfl_up(hlast, 1, L);
-            T F = LT::zero();
+            T hd = __shfl_up_sync(FULL, hlast, 1, L);
+            T F = k.xzero;
             if (has_prev) {
                 int bh[CELLS], bf[CELLS];
 #pragma unroll
@@ -117,85 +119,102 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                 }
                 if (gl == 0) {
                     hd = hb_prev;
-                    F = LT::pack(bf);
+                    F = LT::x_pack(bf);
                 }
-                hb_prev = LT::pack(bh);
+                hb_prev = LT::x_pack(bh);
             } else if (gl == 0) {
-                hd = negO;
+                hd = k.xinit;
             }
 
+            T hpair = k.hzero;  // h of the previous (even) position, for vimax3
             if constexpr (!LAZY) {
-                if (__any_sync(FULL, LT::any_pos(c_prev))) {
-                    // deferred correction by the previous column's carry
-                    T d = LT::add(c_prev, negO);
+                if (__any_sync(FULL, LT::carry_pos(c_prev, k))) {
+                    // deferred correction by the previous column's carry:
+                    // d_j = carry - o - j*e raises E[j] and the diagonal
+                    T d = LT::d0_of(c_prev, k);
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
                         const T Ej = LT::max2(E[j], d);
-                        const T h = LT::addmax_relu(hd, P[j], Ej);
-                        hd = LT::max2(Ho[j], d);
-                        d = LT::add(d, negE);
-                        const T ho = LT::add(h, negO);
-                        Ho[j] = LT::addmax(F, negO, ho);
-                        E[j] = LT::addmax(Ej, negE, Ho[j]);
-                        F = LT::addmax(F, negE, ho);
-                        mx = LT::max2(mx, h);
+                        const T h = LT::h_of(hd, P[j], Ej, k);
+                        hd = LT::xd_corr(X[j], d, k);
+                        d = LT::dstep(d, k);
+                        const T ho = LT::ho_of(h, k);
+                        X[j] = LT::addmax(F, k.negO, ho);
+                        E[j] = LT::e_next(Ej, X[j], k);
+                        F = LT::addmax(F, k.negE, ho);
+                        if (j & 1)
+                            mx = LT::max3(mx, hpair, h);
+                        else if (j == S - 1)
+                            mx = LT::max2(mx, h);
+                        else
+                            hpair = h;
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
-                        const T h = LT::addmax_relu(hd, P[j], E[j]);
-                        hd = Ho[j];
-                        const T ho = LT::add(h, negO);
-                        Ho[j] = LT::addmax(F, negO, ho);
-                        E[j] = LT::addmax(E[j], negE, Ho[j]);
-                        F = LT::addmax(F, negE, ho);
-                        mx = LT::max2(mx, h);
+                        const T h = LT::h_of(hd, P[j], E[j], k);
+                        hd = X[j];
+                        const T ho = LT::ho_of(h, k);
+                        X[j] = LT::addmax(F, k.negO, ho);
+                        E[j] = LT::e_next(E[j], X[j], k);
+                        F = LT::addmax(F, k.negE, ho);
+                        if (j & 1)
+                            mx = LT::max3(mx, hpair, h);
+                        else if (j == S - 1)
+                            mx = LT::max2(mx, h);
+                        else
+                            hpair = h;
                     }
                 }
-                // max-plus prefix scan of the F leaving each lane
+                // max-plus prefix scan of the F leaving each lane (log2 L steps)
                 T x = F;
 #pragma unroll
-                for (int dd = 1; dd < L; dd <<= 1) {
-                    const T y = LT::shfl_up(x, dd, L);
-                    x = LT::addmax(y, LT::splat(-dd * S * e), x);
+                for (int i = 0; i < LOGL; ++i) {
+                    const T y = __shfl_up_sync(FULL, x, 1 << i, L);
+                    x = LT::addmax(y, negW[i], x);
                 }
-                T cin = LT::shfl_up(x, 1, L);
+                T cin = __shfl_up_sync(FULL, x, 1, L);
                 if (gl == 0)
-                    cin = LT::zero();
+                    cin = k.xzero;
                 c_prev = cin;
-                // two adds: each constant stays inside the lane range, so a
-                // saturating lane floors at -128 instead of wrapping
-                hlast = LT::max2(Ho[S - 1], LT::add(LT::add(cin, negO), negS1));
+                hlast = LT::last_corr(X[S - 1], cin, k);
                 if (has_next && gl == L - 1) {
 #pragma unroll
                     for (int c = 0; c < CELLS; ++c)
                         if (r < len[c])
-                            bnd[start[c] + r] = make_int2(LT::get(hlast, c), LT::get(x, c));
+                            bnd[start[c] + r] = make_int2(LT::x_true(hlast, c), LT::x_true(x, c));
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
-                    const T h = LT::addmax_relu(hd, P[j], E[j]);
-                    hd = Ho[j];
-                    const T ho = LT::add(h, negO);
-                    Ho[j] = LT::addmax(F, negO, ho);
-                    E[j] = LT::addmax(E[j], negE, Ho[j]);
-                    F = LT::addmax(F, negE, ho);
-                    mx = LT::max2(mx, h);
+                    const T h = LT::h_of(hd, P[j], E[j], k);
+                    hd = X[j];
+                    const T ho = LT::ho_of(h, k);
+                    X[j] = LT::addmax(F, k.negO, ho);
+                    E[j] = LT::e_next(E[j], X[j], k);
+                    F = LT::addmax(F, k.negE, ho);
+                    if (j & 1)
+                        mx = LT::max3(mx, hpair, h);
+                    else if (j == S - 1)
+                        mx = LT::max2(mx, h);
+                    else
+                        hpair = h;
                 }
-                // lazy-F: shift the carry into the next lane and correct
+                // lazy-F (Alg. 1): shift the carry into the next lane and
+                // correct, for at most L rounds (int32 lanes: X-space and
+                // h-space coincide)
                 T fb = F;  // F leaving this lane, corrected as rounds pass
-                T Fc = LT::shfl_up(F, 1, L);
+                T Fc = __shfl_up_sync(FULL, F, 1, L);
                 if (gl == 0)
-                    Fc = LT::zero();
+                    Fc = k.xzero;
                 bool done = false;
-                for (int k = 0; k < L && !done; ++k) {
+                for (int kk = 0; kk < L && !done; ++kk) {
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
-                        const T hold = Ho[j];
-                        Ho[j] = LT::addmax(Fc, negO, hold);
-                        E[j] = LT::max2(E[j], Ho[j]);
-                        Fc = LT::add(Fc, negE);
+                        const T hold = X[j];
+                        X[j] = LT::addmax(Fc, k.negO, hold);
+                        E[j] = LT::max2(E[j], X[j]);
+                        Fc = Fc + k.negE;  // plain add: this loop is latency-bound
                         ++lazy_steps;
                         if (__all_sync(FULL, Fc <= max(hold, 0))) {
                             done = true;
@@ -204,27 +223,58 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                     }
                     if (!done) {
                         fb = LT::max2(fb, Fc);
-                        Fc = LT::shfl_up(Fc, 1, L);
+                        Fc = __shfl_up_sync(FULL, Fc, 1, L);
                         if (gl == 0)
-                            Fc = LT::zero();
+                            Fc = k.xzero;
                     }
                 }
-                hlast = Ho[S - 1];
+                hlast = X[S - 1];
                 if (has_next && gl == L - 1 && r < len[0])
-                    bnd[start[0] + r] = make_int2(LT::get(hlast, 0), LT::get(fb, 0));
+                    bnd[start[0] + r] = make_int2(LT::x_true(hlast, 0), LT::x_true(fb, 0));
             }
         }
     }
 #pragma unroll
     for (int dd = L / 2; dd >= 1; dd >>= 1)
-        mx = LT::max2(mx, LT::shfl_xor(mx, dd, L));
+        mx = LT::max2(mx, __shfl_xor_sync(FULL, mx, dd, L));
     return mx;
 }
 
-// Stage one striped profile (biased by +o) into shared memory in the layout
-// load_profile reads: [residue][SP / VEC][lane][VEC].  value(a, l, j) gives
-// the raw score of residue a at lane l, segment index j (j < S) or a
-// sentinel below -256 for positions past the query end; row A is inert.
+// Scores of one unit: lane results decoded to true values (combined with
+// the previous chunks' maximum), and for lane types whose cells can leak
+// into each other after an overflow, every cell of a register raised to
+// the flag threshold once one of them reached it.
+template <class LT>
+__device__ __forceinline__ void write_scores(typename LT::T mx, const typename LT::K &k, const int *seq,
+                                             bool has_prev, int32_t flag_thresh, int32_t *scores)
+{
+    constexpr int CELLS = LT::CELLS;
+    int s[CELLS];
+    bool flag = false;
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+        s[c] = LT::score(mx, c, k);
+        if (seq[c] >= 0) {
+            if (has_prev)
+                s[c] = max(s[c], scores[seq[c]]);
+            flag |= s[c] >= flag_thresh;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+        if (seq[c] >= 0) {
+            if (LT::CROSS && flag)
+                s[c] = max(s[c], flag_thresh);
+            scores[seq[c]] = s[c];
+        }
+    }
+}
+
+// Stage one striped profile (biased by the lane type's profile bias) into
+// shared memory in the layout load_profile reads: [residue][SP/VEC][lane][VEC].
+// value(a, l, j) gives the raw score of residue a at lane l, segment index j
+// (j < S) or a sentinel below -256 for positions past the query end; row A
+// is inert.
 template <class LT, int L, int S, class ValueFn>
 __device__ __forceinline__ void stage_profile(typename LT::Elem *dst, int A, int o, int tid, int nthreads,
                                               ValueFn value)
@@ -241,7 +291,7 @@ __device__ __forceinline__ void stage_profile(typename LT::Elem *dst, int A, int
         if (a < A && j < S) {
             const int raw = value(a, l, j);
             if (raw > -256)
-                v = raw + o;
+                v = raw + LT::prof_bias(o);
         }
         dst[((a * (SP / V) + j / V) * L + l) * V + (j % V)] = (typename LT::Elem)v;
     }
@@ -305,19 +355,10 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
             my_n = max(my_n, len[c]);
         }
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
-        const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, has_prev,
-                                                  has_next, p.bnd, gl, lazy_steps);
-        if (gl == 0) {
-#pragma unroll
-            for (int c = 0; c < CELLS; ++c) {
-                if (seq[c] >= 0) {
-                    int s = LT::get(mx, c);
-                    if (has_prev)
-                        s = max(s, p.scores[seq[c]]);
-                    p.scores[seq[c]] = s;
-                }
-            }
-        }
+        const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
+                                                  has_prev, has_next, p.bnd, gl, lazy_steps);
+        if (gl == 0)
+            write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), seq, has_prev, p.flag_thresh, p.scores);
     }
     // j-steps of the correction loop, counted once per warp
     if (LAZY && p.lazy_steps && lane == 0 && lazy_steps)

@@ -30,6 +30,8 @@ struct BatchArgs {
     int32_t *scores;          // per sequence
     uint32_t *counter;        // work counter, zero at launch
     unsigned long long *lazy_steps;  // optional statistics of the lazy-F loop
+    uint32_t one;             // 1 (a run-time multiplier for FMA-pipe additions)
+    int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
 };
 
 // Parameters of the pair kernel (each pair has its own query).
@@ -45,6 +47,8 @@ struct PairArgs {
     int8_t M[32 * 32];          // substitution matrix [query][reference]
     int32_t *scores;
     uint32_t *counter;
+    uint32_t one;             // 1 (a run-time multiplier for FMA-pipe additions)
+    int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
 };
 
 // batch launchers (sw_k_i32.cu, sw_k_i16.cu, sw_k_i8.cu), declared in
@@ -80,8 +84,8 @@ int launch_length_order(const int64_t *off, int64_t n, int32_t *order, int32_t *
 int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32_t *list, int32_t *count,
                          cudaStream_t st, int num_sms);
 
-// Integer-op throughput probe for the ALU roofline: 'op' selects the
-// instruction stream; returns ops executed (lane-ops) and elapsed ms.
-int run_int_peak(int op, int blocks, int threads, int iters, double *lane_ops, float *ms, cudaStream_t st);
+// Cell-rate probe of the plain pass for the roofline: 'op' selects the
+// lane type (0 int32, 1 s16x2, 2 s8x4); returns cells updated and ms.
+int run_int_peak(int op, int blocks, int threads, int iters, double *cells, float *ms, cudaStream_t st);
 
 }  // namespace swg

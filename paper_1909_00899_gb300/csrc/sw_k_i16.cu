@@ -9,8 +9,11 @@ int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream
     if (pl.L == LL && pl.S == SS)                 \
         return launch_batch_inst<LaneI16x2, LL, SS, false>(a, num_sms, st);
     SWG_CASE(8, 8)
+    SWG_CASE(8, 16)
     SWG_CASE(16, 8)
+    SWG_CASE(16, 16)
     SWG_CASE(32, 8)
+    SWG_CASE(32, 12)
     SWG_CASE(32, 16)
 #undef SWG_CASE
     return (int)cudaErrorInvalidValue;

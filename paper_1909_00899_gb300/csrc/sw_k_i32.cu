@@ -11,8 +11,11 @@ int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
                     : launch_batch_inst<LaneI32, LL, SS, false>(a, num_sms, st);
     SWG_CASE(4, 8)
     SWG_CASE(8, 8)
+    SWG_CASE(8, 16)
     SWG_CASE(16, 8)
+    SWG_CASE(16, 16)
     SWG_CASE(32, 8)
+    SWG_CASE(32, 12)
     SWG_CASE(32, 16)
 #undef SWG_CASE
     return (int)cudaErrorInvalidValue;

@@ -1,45 +1,98 @@
 // Lane types of the striped kernels: how one 32-bit register carries the
-// cells of 1, 2 or 4 alignments, and the max-plus primitives on them.
+// cells of 1, 2 or 4 alignments, and the cell update written for them.
 //
-// Every value the recurrence keeps is bounded below by -o (E, F and the
-// stored H - o are all maxed with a value >= -o), and "+ profile" is floored
-// at 0 by the relu forms, which is the signed restatement of the saturating
-// unsigned arithmetic of Sec. I ("none of the vector values can be
-// negative").  Packed lanes are exact until an addition H + M leaves the
-// lane range; such alignments are detected by their maximum (see the
-// overflow threshold in sw_internal.h) and rescored in int32.
+// Value spaces.  The kernels keep X = H - o (the stored H of Alg. 6), E and
+// F, all bounded below by -o, and h = H before F (Alg. 6 takes Max on it).
+// A lane type stores X, F and the scan carries in "X-space" (true + BX) and
+// h, E and the deferred correction d in "h-space" (true + BH), and stages
+// the profile biased by PB (added to every matrix entry):
+//     h = max(Xd + P', E, floor)  is exact when  BH = BX + PB - o.
+// int32 and s8x4 lanes use BX = BH = 0, PB = o and the relu forms, the
+// signed restatement of the paper's saturating arithmetic ("none of the
+// vector values can be negative").  s16x2 lanes use BX = 4096 and PB = 128:
+// every stored half is then a positive 15-bit number, so a plain 32-bit add
+// of a packed constant is an exact add in both halves.
+//
+// Pure additions go through fadd(): IMAD with a multiplier that is 1 at run
+// time, i.e. on the FMA pipe, which leaves the half-rate integer ALU pipe to
+// the max-plus DPX steps.  ALU instructions per register-cell of the plain
+// pass: h (1), X (1), E (1), F (1) and the running max (1/2, vimax3 over two
+// positions); the deferred correction adds 2 (raise E, raise the diagonal).
+//
+// Packed lanes are exact until H + M leaves the lane range.  The H of the
+// first such addition was exact and already folded into the alignment's
+// maximum, so alignments whose packed maximum reached the lane's threshold
+// are rescored in int32 (sw_batch.cuh).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace swg {
 
+// a + b on the FMA pipe: IMAD with a multiplier the compiler cannot fold
+__device__ __forceinline__ uint32_t fadd_u32(uint32_t a, uint32_t one, uint32_t b)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(b));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
 struct LaneI32 {
     using T = int32_t;
     using Elem = int32_t;               // shared-memory profile element
     static constexpr int CELLS = 1;     // alignments per register
     static constexpr int VEC = 4;       // profile elements per 16 bytes
-    static constexpr int PAD = -(1 << 24);  // inert profile score
-    static constexpr int CEIL = 0x3fffffff;
+    static constexpr int PAD = -(1 << 24);  // inert staged profile value
+    static constexpr bool CROSS = false;    // cells never leak into each other
+    __host__ __device__ static constexpr int prof_bias(int o) { return o; }
 
+    struct K {
+        uint32_t one;
+        T negO, negE, negOS1, xzero, hzero, xinit;
+    };
+    __device__ __forceinline__ static K consts(int o, int e, int S, uint32_t one)
+    {
+        K k;
+        k.one = one;
+        k.negO = -o;
+        k.negE = -e;
+        k.negOS1 = -o - (S - 1) * e;
+        k.xzero = 0;   // inert carry / F
+        k.hzero = 0;   // H = 0 in h-space
+        k.xinit = -o;  // X of H = 0
+        return k;
+    }
     __device__ __forceinline__ static T splat(int v) { return v; }
-    __device__ __forceinline__ static T zero() { return 0; }
-    // max(a + b, c, 0)
-    __device__ __forceinline__ static T addmax_relu(T a, T b, T c) { return __viaddmax_s32_relu(a, b, c); }
-    // max(a + b, c)
+    __device__ __forceinline__ static T fadd(T a, T b, const K &k)
+    {
+        return (T)fadd_u32((uint32_t)a, k.one, (uint32_t)b);
+    }
     __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s32(a, b, c); }
-    __device__ __forceinline__ static T add(T a, T b) { return a + b; }
     __device__ __forceinline__ static T max2(T a, T b) { return max(a, b); }
     __device__ __forceinline__ static T max3(T a, T b, T c) { return __vimax3_s32(a, b, c); }
-    __device__ __forceinline__ static bool any_pos(T a) { return a > 0; }
-    __device__ __forceinline__ static int get(T a, int) { return a; }
-    __device__ __forceinline__ static T shfl_up(T a, int d, int w) { return __shfl_up_sync(0xffffffffu, a, d, w); }
-    __device__ __forceinline__ static T shfl_xor(T a, int d, int w) { return __shfl_xor_sync(0xffffffffu, a, d, w); }
-    __device__ __forceinline__ static T pack(const int *v) { return v[0]; }
 
-    // Profile rows of the residues res[c] (one per cell) for segment
-    // positions 0..S-1.  base[c] is cell c's profile, layout
-    // [residue][SP / VEC][lane][VEC] with SP = S rounded up to VEC.
+    // h = max(Xd + P', E, 0)
+    __device__ __forceinline__ static T h_of(T xd, T P, T E, const K &) { return __viaddmax_s32_relu(xd, P, E); }
+    // H' - o in X-space
+    __device__ __forceinline__ static T ho_of(T h, const K &k) { return fadd(h, k.negO, k); }
+    // E of the next column: max(E - e, X)
+    __device__ __forceinline__ static T e_next(T E, T X, const K &k) { return __viaddmax_s32(E, k.negE, X); }
+    // correction value of position 0 (h-space) from a carry (X-space)
+    __device__ __forceinline__ static T d0_of(T c, const K &k) { return fadd(c, k.negO, k); }
+    __device__ __forceinline__ static T dstep(T d, const K &k) { return fadd(d, k.negE, k); }
+    // corrected diagonal (X-space) from the stored X and d (h-space)
+    __device__ __forceinline__ static T xd_corr(T X, T d, const K &) { return max(X, d); }
+    __device__ __forceinline__ static bool carry_pos(T c, const K &) { return c > 0; }
+    // last position raised by the carry: max(X, c - o - (S-1)e)
+    __device__ __forceinline__ static T last_corr(T X, T c, const K &k) { return max(X, fadd(c, k.negOS1, k)); }
+
+    __device__ __forceinline__ static int score(T mx, int, const K &) { return mx; }
+    __device__ __forceinline__ static int x_true(T v, int) { return v; }
+    __device__ __forceinline__ static T x_pack(const int *v) { return v[0]; }
+
+    // Profile rows of residues res[c] for segment positions 0..S-1; base[c]
+    // is cell c's staged profile, layout [residue][SP/VEC][lane][VEC].
     template <int L, int S, int SP>
     __device__ __forceinline__ static void load_profile(const Elem *const *base, const int *res, int gl, T *P)
     {
@@ -55,37 +108,87 @@ struct LaneI32 {
     }
 };
 
+// ---------------------------------------------------------------------------
 struct LaneI16x2 {
     using T = uint32_t;
     using Elem = int16_t;
     static constexpr int CELLS = 2;
     static constexpr int VEC = 8;
-    static constexpr int PAD = -16384;
-    static constexpr int CEIL = 32767;
+    static constexpr int PB = 128;   // staged profile values M + 128, in [0, 255]
+    static constexpr int PAD = 0;    // inert staged value (as if M = -128)
+    static constexpr int BX = 4096;  // X-space bias
+    // the 32-bit adds are exact only while both halves stay in [0, 0x7fff];
+    // once one cell has overflowed the other may be corrupted, so both cells
+    // of a register are rescored together
+    static constexpr bool CROSS = true;
+    __host__ __device__ static constexpr int prof_bias(int) { return PB; }
 
-    // constants saturate to the lane range
+    struct K {
+        uint32_t one;
+        int bh;
+        T negO, negE, delta, negDelta, xzero, hzero, xinit;
+        T hshift32, negE32, d0c32, negOS1_32;
+    };
+    // per-half constant for the DPX forms (saturated to 16 bits)
     __device__ __forceinline__ static T splat(int v)
     {
         v = max(-32768, min(32767, v));
         return (uint32_t)(v & 0xffff) * 0x10001u;
     }
-    __device__ __forceinline__ static T zero() { return 0u; }
-    __device__ __forceinline__ static T addmax_relu(T a, T b, T c) { return __viaddmax_s16x2_relu(a, b, c); }
+    // constant whose 32-bit add adds v to both halves
+    __device__ __forceinline__ static T splat32(int v) { return (uint32_t)v * 65537u; }
+    __device__ __forceinline__ static K consts(int o, int e, int S, uint32_t one)
+    {
+        K k;
+        k.one = one;
+        k.bh = BX + PB - o;
+        k.negO = splat(-o);
+        k.negE = splat(-e);
+        k.delta = splat(k.bh - BX);
+        k.negDelta = splat(BX - k.bh);
+        k.xzero = splat(BX);
+        k.hzero = splat(k.bh);
+        k.xinit = splat(BX - o);
+        k.hshift32 = splat32(-PB);              // h -> H' - o in X-space
+        k.negE32 = splat32(-e);
+        k.d0c32 = splat32(k.bh - BX - o);       // carry (X) -> d (h): c - o
+        k.negOS1_32 = splat32(-o - (S - 1) * e);
+        return k;
+    }
+    __device__ __forceinline__ static T fadd(T a, T b, const K &k) { return fadd_u32(a, k.one, b); }
     __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s16x2(a, b, c); }
-    // a + b per half; the floor 0x8000 never binds for the bounded values used here
-    __device__ __forceinline__ static T add(T a, T b) { return __viaddmax_s16x2(a, b, 0x80008000u); }
     __device__ __forceinline__ static T max2(T a, T b) { return __vmaxs2(a, b); }
     __device__ __forceinline__ static T max3(T a, T b, T c) { return __vimax3_s16x2(a, b, c); }
-    __device__ __forceinline__ static bool any_pos(T a)
+
+    __device__ __forceinline__ static T h_of(T xd, T P, T E, const K &k)
     {
-        return (int16_t)(a & 0xffffu) > 0 || (int16_t)(a >> 16) > 0;
+        return __vimax3_s16x2(fadd(xd, P, k), E, k.hzero);
     }
-    __device__ __forceinline__ static int get(T a, int c) { return (int)(int16_t)(c ? (a >> 16) : (a & 0xffffu)); }
-    __device__ __forceinline__ static T shfl_up(T a, int d, int w) { return __shfl_up_sync(0xffffffffu, a, d, w); }
-    __device__ __forceinline__ static T shfl_xor(T a, int d, int w) { return __shfl_xor_sync(0xffffffffu, a, d, w); }
-    __device__ __forceinline__ static T pack(const int *v)
+    __device__ __forceinline__ static T ho_of(T h, const K &k) { return fadd(h, k.hshift32, k); }
+    __device__ __forceinline__ static T e_next(T E, T X, const K &k)
     {
-        return (uint32_t)(v[0] & 0xffff) | ((uint32_t)(v[1] & 0xffff) << 16);
+        return __viaddmax_s16x2(X, k.delta, fadd(E, k.negE32, k));
+    }
+    __device__ __forceinline__ static T d0_of(T c, const K &k) { return fadd(c, k.d0c32, k); }
+    __device__ __forceinline__ static T dstep(T d, const K &k) { return fadd(d, k.negE32, k); }
+    __device__ __forceinline__ static T xd_corr(T X, T d, const K &k) { return __viaddmax_s16x2(d, k.negDelta, X); }
+    __device__ __forceinline__ static bool carry_pos(T c, const K &)
+    {
+        return (int)(c & 0xffffu) > BX || (int)(c >> 16) > BX;
+    }
+    __device__ __forceinline__ static T last_corr(T X, T c, const K &k)
+    {
+        return __vmaxs2(X, fadd(c, k.negOS1_32, k));
+    }
+
+    __device__ __forceinline__ static int score(T mx, int c, const K &k)
+    {
+        return (int)(int16_t)(c ? (mx >> 16) : (mx & 0xffffu)) - k.bh;
+    }
+    __device__ __forceinline__ static int x_true(T v, int c) { return (int)(int16_t)(c ? (v >> 16) : (v & 0xffffu)) - BX; }
+    __device__ __forceinline__ static T x_pack(const int *v)
+    {
+        return (uint32_t)((v[0] + BX) & 0xffff) | ((uint32_t)((v[1] + BX) & 0xffff) << 16);
     }
 
     template <int L, int S, int SP>
@@ -108,40 +211,65 @@ struct LaneI16x2 {
     }
 };
 
+// ---------------------------------------------------------------------------
 struct LaneI8x4 {
     using T = uint32_t;
     using Elem = int8_t;
     static constexpr int CELLS = 4;
     static constexpr int VEC = 16;
     static constexpr int PAD = -128;
-    static constexpr int CEIL = 127;
+    static constexpr bool CROSS = false;  // saturating bytes never leak
+    __host__ __device__ static constexpr int prof_bias(int o) { return o; }
 
-    // constants saturate to the lane range: a clamped negative weight gives
-    // a saturated sum <= max(true sum, -128), which is inert wherever the
-    // true sum was (every kept value is >= -o >= -127)
+    struct K {
+        T negO, negE, negS1, xzero, hzero, xinit;
+    };
+    // constants saturate to the lane range: a clamped negative constant
+    // gives a saturated sum <= max(true sum, -128), which is inert wherever
+    // the true sum was (every kept value is >= -o >= -127)
     __device__ __forceinline__ static T splat(int v)
     {
         v = max(-128, min(127, v));
         return (uint32_t)(v & 0xff) * 0x01010101u;
     }
-    __device__ __forceinline__ static T zero() { return 0u; }
-    // saturating byte adds: a sum above 127 pins at 127 and flags the alignment
-    __device__ __forceinline__ static T addmax_relu(T a, T b, T c)
+    __device__ __forceinline__ static K consts(int o, int e, int S, uint32_t)
     {
-        return __vmaxs4(__vmaxs4(__vaddss4(a, b), c), 0u);
+        K k;
+        k.negO = splat(-o);
+        k.negE = splat(-e);
+        k.negS1 = splat(-(S - 1) * e);
+        k.xzero = 0u;
+        k.hzero = 0u;
+        k.xinit = splat(-o);
+        return k;
     }
+    __device__ __forceinline__ static T fadd(T a, T b, const K &) { return __vaddss4(a, b); }
     __device__ __forceinline__ static T addmax(T a, T b, T c) { return __vmaxs4(__vaddss4(a, b), c); }
-    __device__ __forceinline__ static T add(T a, T b) { return __vaddss4(a, b); }
     __device__ __forceinline__ static T max2(T a, T b) { return __vmaxs4(a, b); }
     __device__ __forceinline__ static T max3(T a, T b, T c) { return __vmaxs4(__vmaxs4(a, b), c); }
-    __device__ __forceinline__ static bool any_pos(T a)
+
+    __device__ __forceinline__ static T h_of(T xd, T P, T E, const K &)
     {
-        return (int8_t)a > 0 || (int8_t)(a >> 8) > 0 || (int8_t)(a >> 16) > 0 || (int8_t)(a >> 24) > 0;
+        return __vmaxs4(__vmaxs4(__vaddss4(xd, P), E), 0u);
     }
-    __device__ __forceinline__ static int get(T a, int c) { return (int)(int8_t)(a >> (8 * c)); }
-    __device__ __forceinline__ static T shfl_up(T a, int d, int w) { return __shfl_up_sync(0xffffffffu, a, d, w); }
-    __device__ __forceinline__ static T shfl_xor(T a, int d, int w) { return __shfl_xor_sync(0xffffffffu, a, d, w); }
-    __device__ __forceinline__ static T pack(const int *v)
+    __device__ __forceinline__ static T ho_of(T h, const K &k) { return __vaddss4(h, k.negO); }
+    __device__ __forceinline__ static T e_next(T E, T X, const K &k) { return __vmaxs4(__vaddss4(E, k.negE), X); }
+    __device__ __forceinline__ static T d0_of(T c, const K &k) { return __vaddss4(c, k.negO); }
+    __device__ __forceinline__ static T dstep(T d, const K &k) { return __vaddss4(d, k.negE); }
+    __device__ __forceinline__ static T xd_corr(T X, T d, const K &) { return __vmaxs4(X, d); }
+    __device__ __forceinline__ static bool carry_pos(T c, const K &)
+    {
+        return (int8_t)c > 0 || (int8_t)(c >> 8) > 0 || (int8_t)(c >> 16) > 0 || (int8_t)(c >> 24) > 0;
+    }
+    // two saturating adds: each constant stays in range, the result floors at -128
+    __device__ __forceinline__ static T last_corr(T X, T c, const K &k)
+    {
+        return __vmaxs4(X, __vaddss4(__vaddss4(c, k.negO), k.negS1));
+    }
+
+    __device__ __forceinline__ static int score(T mx, int c, const K &) { return (int)(int8_t)(mx >> (8 * c)); }
+    __device__ __forceinline__ static int x_true(T v, int c) { return (int)(int8_t)(v >> (8 * c)); }
+    __device__ __forceinline__ static T x_pack(const int *v)
     {
         return (uint32_t)(v[0] & 0xff) | ((uint32_t)(v[1] & 0xff) << 8) | ((uint32_t)(v[2] & 0xff) << 16) |
                ((uint32_t)(v[3] & 0xff) << 24);

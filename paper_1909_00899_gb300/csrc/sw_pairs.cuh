@@ -88,21 +88,17 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
                 for (int a = 0; a <= A; ++a) {
                     int v = LT::PAD;
                     if (code >= 0 && a < A)
-                        v = (int)p.M[code * A + a] + p.o;
+                        v = (int)p.M[code * A + a] + LT::prof_bias(p.o);
                     dst[((a * (SP / V) + j / V) * L + l) * V + (j % V)] = (Elem)v;
                 }
             }
         }
         __syncwarp(FULL);
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
-        const T mx = striped_unit<LT, L, S, false>(pbase, p.r, start, len, ncols, A, p.o, p.e, false, false,
-                                                   nullptr, gl, unused);
-        if (gl == 0) {
-#pragma unroll
-            for (int c = 0; c < CELLS; ++c)
-                if (pid[c] >= 0)
-                    p.scores[pid[c]] = LT::get(mx, c);
-        }
+        const T mx = striped_unit<LT, L, S, false>(pbase, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
+                                                   false, nullptr, gl, unused);
+        if (gl == 0)
+            write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), pid, false, p.flag_thresh, p.scores);
         __syncwarp(FULL);  // profiles are rewritten by the next unit
     }
 }

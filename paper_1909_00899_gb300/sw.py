@@ -28,9 +28,10 @@ SW_LANE_I8X4 = 3
 
 # every function declared in include/sw_gb300.h
 EXPORTS = (
-    "sw_profile_build", "sw_profile_free", "sw_profile_plan", "sw_align_batch",
+    "sw_profile_build", "sw_profile_build_ex", "sw_profile_free", "sw_profile_free_async", "sw_profile_plan", "sw_align_batch",
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
-    "sw_probe_cell_rate", "sw_version",
+    "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
+    "sw_align_lazyf_db",
 )
 
 
@@ -56,8 +57,12 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         L.sw_profile_build.restype = ctypes.c_int
         L.sw_profile_build.argtypes = [_vp, _i32, _vp, _i32, _i32, _vp, ctypes.POINTER(_vp)]
+        L.sw_profile_build_ex.restype = ctypes.c_int
+        L.sw_profile_build_ex.argtypes = [_vp, _i32, _vp, _i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]
         L.sw_profile_free.restype = ctypes.c_int
         L.sw_profile_free.argtypes = [_vp]
+        L.sw_profile_free_async.restype = ctypes.c_int
+        L.sw_profile_free_async.argtypes = [_vp, _vp]
         L.sw_profile_plan.restype = ctypes.c_int
         L.sw_profile_plan.argtypes = [_vp] + [ctypes.POINTER(_i32)] * 4
         for name in ("sw_align_batch", "sw_align_lazyf_batch"):
@@ -66,6 +71,14 @@ def lib():
             f.argtypes = [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp]
         L.sw_align_pairs.restype = ctypes.c_int
         L.sw_align_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
+        L.sw_db_create.restype = ctypes.c_int
+        L.sw_db_create.argtypes = [_vp, _vp, _i64, _vp, ctypes.POINTER(_vp)]
+        L.sw_db_free.restype = ctypes.c_int
+        L.sw_db_free.argtypes = [_vp]
+        for name in ("sw_align_db", "sw_align_lazyf_db"):
+            f = getattr(L, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
         L.sw_stream_sync.restype = ctypes.c_int
         L.sw_stream_sync.argtypes = [_vp, _i64]
         L.sw_last_error.restype = ctypes.c_char_p
@@ -108,7 +121,7 @@ def _dev_ptr(t, dtype_name):
 class Profile:
     """Owns a device profile built by sw_profile_build."""
 
-    def __init__(self, query, subst_matrix, lane_type=SW_LANE_AUTO, stream=None):
+    def __init__(self, query, subst_matrix, lane_type=SW_LANE_AUTO, stream=None, lanes=0, seg_len=0):
         q = np.ascontiguousarray(query, dtype=np.uint8)
         M = np.ascontiguousarray(subst_matrix, dtype=np.int8)
         if M.ndim != 2 or M.shape[0] != M.shape[1]:
@@ -116,9 +129,9 @@ class Profile:
         self.qlen = int(q.size)
         self.alphabet = int(M.shape[0])
         h = _vp()
-        _check(lib().sw_profile_build(q.ctypes.data if q.size else None, self.qlen,
-                                      M.ctypes.data, self.alphabet, lane_type,
-                                      _stream(stream), ctypes.byref(h)))
+        _check(lib().sw_profile_build_ex(q.ctypes.data if q.size else None, self.qlen,
+                                         M.ctypes.data, self.alphabet, lane_type, int(lanes),
+                                         int(seg_len), _stream(stream), ctypes.byref(h)))
         self._h = h
 
     @property
@@ -132,8 +145,15 @@ class Profile:
                     lane_type=vals[3].value)
 
     def free(self):
+        """Waits for the device, then releases the profile."""
         if getattr(self, "_h", None):
             lib().sw_profile_free(self._h)
+            self._h = None
+
+    def free_async(self, stream=None):
+        """Releases the profile in stream order (no wait)."""
+        if getattr(self, "_h", None):
+            _check(lib().sw_profile_free_async(self._h, _stream(stream)))
             self._h = None
 
     def __del__(self):
@@ -147,8 +167,16 @@ def sw_profile_build(query, subst_matrix, lane_type=SW_LANE_AUTO, stream=None):
     return Profile(query, subst_matrix, lane_type, stream)
 
 
+def sw_profile_build_ex(query, subst_matrix, lane_type, lanes, seg_len, stream=None):
+    return Profile(query, subst_matrix, lane_type, stream, lanes, seg_len)
+
+
 def sw_profile_free(profile):
     profile.free()
+
+
+def sw_profile_free_async(profile, stream=None):
+    profile.free_async(stream)
 
 
 def _align(fn, profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream):
@@ -185,6 +213,60 @@ def sw_align_pairs(q, q_off, r, r_off, subst_matrix, gap_open, gap_extend, score
                                 _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
                                 int(gap_open), int(gap_extend), int(lane_type),
                                 _dev_ptr(scores_out, "int32"), _stream(stream)))
+    return scores_out
+
+
+class Database:
+    """A device-resident database (sw_db): keeps references to the residue
+    and offset tensors, which must stay alive while the handle exists."""
+
+    def __init__(self, db_residues, db_offsets, stream=None):
+        self.residues = db_residues
+        self.offsets = db_offsets
+        self.n = int(db_offsets.numel()) - 1
+        h = _vp()
+        _check(lib().sw_db_create(_dev_ptr(db_residues, "uint8"), _dev_ptr(db_offsets, "int64"),
+                                  self.n, _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().sw_db_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sw_db_create(db_residues, db_offsets, stream=None):
+    return Database(db_residues, db_offsets, stream)
+
+
+def sw_db_free(db):
+    db.free()
+
+
+def sw_align_db(profile, db, gap_open, gap_extend, scores_out, stream=None):
+    """Scan-F scores against a resident database (graph-capturable)."""
+    if scores_out.numel() < db.n:
+        raise ValueError("scores_out too small")
+    _check(lib().sw_align_db(profile.handle, db.handle, int(gap_open), int(gap_extend),
+                             _dev_ptr(scores_out, "int32"), _stream(stream)))
+    return scores_out
+
+
+def sw_align_lazyf_db(profile, db, gap_open, gap_extend, scores_out, stream=None):
+    if scores_out.numel() < db.n:
+        raise ValueError("scores_out too small")
+    _check(lib().sw_align_lazyf_db(profile.handle, db.handle, int(gap_open), int(gap_extend),
+                                   _dev_ptr(scores_out, "int32"), _stream(stream)))
     return scores_out
 
 
