@@ -28,6 +28,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 QLENS = (128, 512, 2048, 5000)
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
+# capture summarised in profiles/sw_batch_kernel_s16x2_32x32_m2048_100k.md
+# (chunk 0 of an m=2048 query against this database).  Set to None whenever
+# the kernel changes, until it is captured again.
+NCU_TRAFFIC = {"bytes_per_launch": 48.676352e6 + 267.91296e6,
+               "kernel": "sw_batch_kernel<LaneI16x2, 32, 32>", "launch": "m=2048 chunk 0 vs 100k sequences",
+               "source": "profiles/sw_batch_kernel_s16x2_32x32_m2048_100k.md"}
 METRIC = "GCUPS scan-F (bit-exact) vs lazy-F"
 WORKLOAD = ("protein queries m in {128,512,2048,5000} vs 100k db seqs, log-normal lengths "
             "(median 300, sigma 0.76, clip [20,35000]), o=11 e=1")
@@ -49,6 +56,8 @@ def parse():
                     help="comma-separated query lengths (profiling cases)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no oracle check, lazy-F, e2e, probe or CPU baseline")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="CUDA streams the independent queries of a step are spread over")
     return ap.parse_args()
 
 
@@ -224,18 +233,26 @@ def main():
     off_d = torch.from_numpy(w["off"]).cuda()
     outs = [torch.zeros(n_db, dtype=torch.int32, device="cuda") for _ in QLENS]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    side = [torch.cuda.Stream() for _ in range(max(1, args.streams))]
 
-    def step(lazy=False, timers=None):
+    def step(lazy=False):
+        """One pass of the path: every query's profile and its alignment
+        against the whole db; the independent queries are spread over the
+        side streams and joined back into the current stream."""
+        fork = torch.cuda.Event()
+        fork.record(stream)
         profs = []
         for i, q in enumerate(w["queries"]):
-            if timers is not None:
-                timers[i][0].record(stream)
-            p = sw.Profile(q, M, sw.SW_LANE_I32 if lazy else lane, stream=stream)
+            st = side[i % len(side)]
+            st.wait_event(fork)
+            p = sw.Profile(q, M, sw.SW_LANE_I32 if lazy else lane, stream=st)
             fn = sw.sw_align_lazyf_batch if lazy else sw.sw_align_batch
-            fn(p, db_d, off_d, o, e, outs[i], stream=stream)
-            if timers is not None:
-                timers[i][1].record(stream)
+            fn(p, db_d, off_d, o, e, outs[i], stream=st)
             profs.append(p)
+        for st in side:
+            j = torch.cuda.Event()
+            j.record(st)
+            stream.wait_event(j)
         return profs
 
     def timed(nsteps, lazy=False):
@@ -245,63 +262,88 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         total_ms = 0.0
-        per_query = [0.0] * len(QLENS)
         keep = []
         for _ in range(nsteps):
-            flush.zero_()  # L2 flush between timed steps (db is 40 MB < 129 MB L2)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in QLENS]
-            keep.append((step(lazy, ev), ev))
+            flush.zero_()  # L2 flush between timed steps (the db is 40 MB < 129 MB L2)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            profs = step(lazy)
+            b.record(stream)
+            keep.append((profs, a, b))
         torch.cuda.synchronize()
-        for _, ev in keep:
-            for i, (a, b) in enumerate(ev):
-                t = a.elapsed_time(b)
-                per_query[i] += t
-                total_ms += t
+        for _, a, b in keep:
+            total_ms += a.elapsed_time(b)
         if world > 1:
             t = torch.tensor([total_ms], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
-        return total_ms, per_query
+        return total_ms
+
+    def per_query(lazy=False):
+        """Each query's alignment call alone on the current stream, timed
+        with CUDA events on that stream (the dominant kernel's launches)."""
+        ms = []
+        for q, out in zip(w["queries"], outs):
+            p = sw.Profile(q, M, sw.SW_LANE_I32 if lazy else lane, stream=stream)
+            torch.cuda.synchronize()
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            (sw.sw_align_lazyf_batch if lazy else sw.sw_align_batch)(p, db_d, off_d, o, e, out, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            p.free()
+        return ms
 
     # correctness spot check against the oracle on a sample (not timed)
     check = None if args.quick else sample_check(w, outs, step, rank)
 
     sampler = ClockSampler(local)
     sampler.start()
-    total_ms, per_q = timed(args.steps)
+    total_ms = timed(args.steps)
     clocks = sampler.stop()
     gcups = cells_step * args.steps * world / (total_ms * 1e-3) / 1e9
+    per_q = per_query()
 
     lazy = None
     if not args.no_lazyf:
         lsteps = max(1, min(args.steps, 2))
-        lms, lper = timed(lsteps, lazy=True)
+        lms = timed(lsteps, lazy=True)
+        lper = per_query(lazy=True)
         lazy = {"value": cells_step * lsteps / (lms * 1e-3) / 1e9, "unit": "GCUPS",
-                "per_query_gcups": {str(m): sum(QLENS) and m * total_res * lsteps / (t * 1e-3) / 1e9
-                                    for m, t in zip(QLENS, lper)}}
+                "per_query_gcups": {str(m): m * total_res / (t * 1e-3) / 1e9 for m, t in zip(QLENS, lper)}}
 
     # end to end through the public API: host (pinned) inputs copied in,
     # scores copied out, inside the timed region
     e2e = None if args.quick else run_e2e(w, lane, args, stream, cells_step)
 
-    # roofline of the dominant kernel (the scan-F batch kernel)
-    prof0 = sw.Profile(w["queries"][-1], M, lane)
-    plan = prof0.plan()
-    prof0.free()
-    cells_per_op = {1: 1, 2: 2, 3: 4}[plan["lane_type"]]
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    mhz = clocks.get("sm_mhz") or 2070.0
-    peak = sms * 128 * mhz * 1e6 / (6.0 / cells_per_op) / 1e9
-    probe = None if args.quick else sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
+    # roofline of the dominant kernel (the scan-F batch kernel): cells of
+    # each query's call over that call's event-timed duration, all queries
+    plans = []
     launches_per_step = 0
     for m in QLENS:
         pf = sw.Profile(np.zeros(m, np.uint8), M, lane)
         pl = pf.plan()
         pf.free()
-        c32 = -(-m // 512) if m > 256 else 1
+        pf32 = sw.Profile(np.zeros(m, np.uint8), M, sw.SW_LANE_I32)
+        pl32 = pf32.plan()
+        pf32.free()
+        plans.append(pl)
         packed = pl["lane_type"] != sw.SW_LANE_I32
-        launches_per_step += (2 if packed else 1) + 3 + pl["chunks"] + ((1 + c32) if packed else 0)
+        # profile build (+ its int32 twin), 3 order kernels, one launch per
+        # chunk, then for packed lanes the flag kernel and the int32 rescore
+        launches_per_step += (2 if packed else 1) + 3 + pl["chunks"] + ((1 + pl32["chunks"]) if packed else 0)
+    plan = plans[-1]
+    cells_per_op = {1: 1, 2: 2, 3: 4}[plan["lane_type"]]
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    # integer ALU pipe: 16 lanes/clk per SM sub-partition, 4 per SM
+    peak_alu = sms * 64 * mhz * 1e6 / (6.0 / cells_per_op) / 1e9
+    kernel_gcups = sum(QLENS) * total_res / (sum(per_q) * 1e-3) / 1e9
+    probe = None if args.quick else sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
 
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
@@ -309,17 +351,24 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "s16x2+int32" if cells_per_op == 2 else
         ("int32" if cells_per_op == 1 else "s8x4+int32"), "data": "synthetic",
         "config": {"workload": workload, "n_db": n_db, "db_residues": total_res,
-                   "cells_per_step": cells_step, "lane": args.lane, "plan_m5000": plan,
+                   "cells_per_step": cells_step, "lane": args.lane, "plan_longest": plan,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "per_query_gcups": {str(m): m * total_res * args.steps / (t * 1e-3) / 1e9 for m, t in zip(QLENS, per_q)},
+        "per_query_gcups": {str(m): m * total_res / (t * 1e-3) / 1e9 for m, t in zip(QLENS, per_q)},
+        "plans": {str(m): p for m, p in zip(QLENS, plans)},
+        "streams": args.streams,
         "lazyf": lazy,
         "scan_vs_lazyf": (gcups / world / lazy["value"]) if lazy else None,
-        "roofline": {"bound": "alu", "achieved": gcups / world, "peak": peak, "unit": "GCUPS",
-                     "frac": gcups / world / peak, "traffic": None,
-                     "peak_basis": "%d SMs x 128 int32 lane-instr/clk x %.0f MHz (median sampled) / %g instr per cell"
-                                   % (sms, mhz, 6.0 / cells_per_op),
-                     "probe_gcups": probe, "frac_of_probe": (gcups / world / probe) if probe else None},
+        "scan_vs_lazyf_per_query": ({str(m): (m * total_res / (t * 1e-3) / 1e9) / lazy["per_query_gcups"][str(m)]
+                                     for m, t in zip(QLENS, per_q)} if lazy else None),
+        "roofline": {"bound": "alu", "achieved": kernel_gcups, "peak": peak_alu, "unit": "GCUPS",
+                     "frac": kernel_gcups / peak_alu,
+                     "traffic": NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC else None,
+                     "traffic_basis": NCU_TRAFFIC,
+                     "peak_basis": ("%d SMs x 64 int lane-ops/clk (half-rate ALU pipe, 4 x 16 lanes) x %.0f MHz "
+                                    "(median sampled) / %g DPX instr per cell" % (sms, mhz, 6.0 / cells_per_op)),
+                     "achieved_basis": "sum of m*n over each query's sw_align_batch call / its CUDA-event time",
+                     "probe_gcups": probe, "frac_of_probe": (kernel_gcups / probe) if probe else None},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -357,6 +406,10 @@ def sample_check(w, outs, step, rank):
 
 
 def run_e2e(w, lane, args, stream, cells_step):
+    """Same step through the public API from host buffers: the pinned db and
+    offsets are copied in, every query is profiled from host memory and
+    aligned, and its scores are copied back to pinned host memory, all inside
+    the timed region."""
     import torch
 
     from paper_1909_00899_gb300 import sw
@@ -367,16 +420,26 @@ def run_e2e(w, lane, args, stream, cells_step):
     db_d = torch.empty_like(db_h, device="cuda")
     off_d = torch.empty_like(off_h, device="cuda")
     outs = [torch.empty(n_db, dtype=torch.int32, device="cuda") for _ in QLENS]
+    side = [torch.cuda.Stream() for _ in range(max(1, args.streams))]
 
     def one():
         db_d.copy_(db_h, non_blocking=True)
         off_d.copy_(off_h, non_blocking=True)
+        fork = torch.cuda.Event()
+        fork.record(stream)
         profs = []
         for i, q in enumerate(w["queries"]):
-            p = sw.Profile(q, w["M"], lane, stream=stream)
-            sw.sw_align_batch(p, db_d, off_d, w["o"], w["e"], outs[i], stream=stream)
-            out_h[i].copy_(outs[i], non_blocking=True)
+            st = side[i % len(side)]
+            st.wait_event(fork)
+            p = sw.Profile(q, w["M"], lane, stream=st)
+            sw.sw_align_batch(p, db_d, off_d, w["o"], w["e"], outs[i], stream=st)
+            with torch.cuda.stream(st):
+                out_h[i].copy_(outs[i], non_blocking=True)
             profs.append(p)
+        for st in side:
+            j = torch.cuda.Event()
+            j.record(st)
+            stream.wait_event(j)
         return profs
 
     for _ in range(max(1, args.warmup)):

@@ -85,9 +85,9 @@ int sw_profile_build(const uint8_t *query, int32_t qlen,
  * per alignment (the paper's p, a power of two up to 32) and seg_len query
  * positions per lane (segLen); both 0 selects the built-in table.  Only the
  * shapes the kernels are compiled for are accepted (SW_ERR_INVALID
- * otherwise): int32 {4x8, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16},
- * s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16}, s8x4 {8x16, 16x16,
- * 32x16}.  Used by the autotuner.
+ * otherwise): int32 {4x8, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16,
+ * 16x32, 32x32}, s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
+ * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}.  Used by the autotuner.
  */
 int sw_profile_build_ex(const uint8_t *query, int32_t qlen,
                         const int8_t *subst_matrix, int32_t alphabet,

@@ -18,8 +18,9 @@ from . import sw
 BINS = (64, 128, 256, 512, 1024, 2048, 4096, 1 << 30)
 
 CANDIDATES = {
-    sw.SW_LANE_I16X2: ((8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16)),
-    sw.SW_LANE_I32: ((4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16)),
+    sw.SW_LANE_I16X2: ((8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24),
+                       (32, 32)),
+    sw.SW_LANE_I32: ((4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 32)),
 }
 
 

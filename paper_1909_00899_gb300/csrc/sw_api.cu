@@ -105,18 +105,20 @@ struct Choice {
 
 // Lanes per alignment and segment length per lane type, smallest chunk that
 // holds the query first; longer queries use the last entry in chunks.
-const Choice kI32[] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {32, 16}};
-const Choice kI16[] = {{8, 8}, {16, 8}, {32, 8}, {32, 16}};
+// (measured on GB300: the widest segment that keeps padding low wins,
+// 32 lanes x 32 positions for long queries)
+const Choice kI32[] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {32, 16}, {32, 32}};
+const Choice kI16[] = {{8, 8}, {16, 8}, {32, 8}, {32, 16}, {32, 32}};
 const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
 // every (lanes, segment length) the batch kernels are instantiated for
-const Choice kAllI32[] = {{4, 8}, {8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}};
-const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}};
+const Choice kAllI32[] = {{4, 8}, {8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 32}};
+const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
 
 bool plan_supported(int lane, int L, int S)
 {
     const Choice *t = lane == SW_LANE_I32 ? kAllI32 : (lane == SW_LANE_I16X2 ? kAllI16 : kAllI8);
-    const int n = lane == SW_LANE_I32 ? 8 : (lane == SW_LANE_I16X2 ? 7 : 3);
+    const int n = lane == SW_LANE_I32 ? 10 : (lane == SW_LANE_I16X2 ? 10 : 3);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;
@@ -132,10 +134,10 @@ const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4;
 Plan choose_plan(int32_t qlen, int lane)
 {
     const Choice *tab = kI32;
-    int n = 5;
+    int n = 6;
     if (lane == SW_LANE_I16X2) {
         tab = kI16;
-        n = 4;
+        n = 5;
     } else if (lane == SW_LANE_I8X4) {
         tab = kI8;
         n = 3;

@@ -105,8 +105,10 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
 #pragma unroll
             for (int c = 0; c < CELLS; ++c)
                 res[c] = __shfl_sync(FULL, myres[c], rr, L);
-            T P[S];
-            LT::template load_profile<L, S, SP>(pbase, res, gl, P);
+            // the profile is fetched one 16-byte vector (VEC positions) at a
+            // time inside the position loops, so only VEC values are live
+            constexpr int V = LT::VEC;
+            T Pv[V];
 
             T hd = __shfl_up_sync(FULL, hlast, 1, L);
             T F = k.xzero;
@@ -134,8 +136,10 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                     T d = LT::d0_of(c_prev, k);
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
+                        if (j % V == 0)
+                            LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
                         const T Ej = LT::max2(E[j], d);
-                        const T h = LT::h_of(hd, P[j], Ej, k);
+                        const T h = LT::h_of(hd, Pv[j % V], Ej, k);
                         hd = LT::xd_corr(X[j], d, k);
                         d = LT::dstep(d, k);
                         const T ho = LT::ho_of(h, k);
@@ -152,7 +156,9 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                 } else {
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
-                        const T h = LT::h_of(hd, P[j], E[j], k);
+                        if (j % V == 0)
+                            LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
+                        const T h = LT::h_of(hd, Pv[j % V], E[j], k);
                         hd = X[j];
                         const T ho = LT::ho_of(h, k);
                         X[j] = LT::addmax(F, k.negO, ho);
@@ -187,7 +193,9 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
             } else {
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
-                    const T h = LT::h_of(hd, P[j], E[j], k);
+                    if (j % V == 0)
+                        LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
+                    const T h = LT::h_of(hd, Pv[j % V], E[j], k);
                     hd = X[j];
                     const T ho = LT::ho_of(h, k);
                     X[j] = LT::addmax(F, k.negO, ho);

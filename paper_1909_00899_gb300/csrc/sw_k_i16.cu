@@ -15,6 +15,9 @@ int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream
     SWG_CASE(32, 8)
     SWG_CASE(32, 12)
     SWG_CASE(32, 16)
+    SWG_CASE(16, 32)
+    SWG_CASE(32, 24)
+    SWG_CASE(32, 32)
 #undef SWG_CASE
     return (int)cudaErrorInvalidValue;
 }

@@ -93,6 +93,17 @@ struct LaneI32 {
 
     // Profile rows of residues res[c] for segment positions 0..S-1; base[c]
     // is cell c's staged profile, layout [residue][SP/VEC][lane][VEC].
+    // profile vector k (positions VEC*k .. VEC*k+VEC-1) of the residues res[c]
+    template <int L, int SP>
+    __device__ __forceinline__ static void load_vec(const Elem *const *base, const int *res, int gl, int k, T *P)
+    {
+        const int4 v = reinterpret_cast<const int4 *>(base[0])[(res[0] * (SP / 4) + k) * L + gl];
+        P[0] = v.x;
+        P[1] = v.y;
+        P[2] = v.z;
+        P[3] = v.w;
+    }
+
     template <int L, int S, int SP>
     __device__ __forceinline__ static void load_profile(const Elem *const *base, const int *res, int gl, T *P)
     {
@@ -191,6 +202,21 @@ struct LaneI16x2 {
         return (uint32_t)((v[0] + BX) & 0xffff) | ((uint32_t)((v[1] + BX) & 0xffff) << 16);
     }
 
+    template <int L, int SP>
+    __device__ __forceinline__ static void load_vec(const Elem *const *base, const int *res, int gl, int k, T *P)
+    {
+        const int4 a = reinterpret_cast<const int4 *>(base[0])[(res[0] * (SP / 8) + k) * L + gl];
+        const int4 b = reinterpret_cast<const int4 *>(base[1])[(res[1] * (SP / 8) + k) * L + gl];
+        P[0] = __byte_perm(a.x, b.x, 0x5410);
+        P[1] = __byte_perm(a.x, b.x, 0x7632);
+        P[2] = __byte_perm(a.y, b.y, 0x5410);
+        P[3] = __byte_perm(a.y, b.y, 0x7632);
+        P[4] = __byte_perm(a.z, b.z, 0x5410);
+        P[5] = __byte_perm(a.z, b.z, 0x7632);
+        P[6] = __byte_perm(a.w, b.w, 0x5410);
+        P[7] = __byte_perm(a.w, b.w, 0x7632);
+    }
+
     template <int L, int S, int SP>
     __device__ __forceinline__ static void load_profile(const Elem *const *base, const int *res, int gl, T *P)
     {
@@ -286,6 +312,19 @@ struct LaneI8x4 {
         P[1] = __byte_perm(ab_lo, cd_lo, 0x7632);
         P[2] = __byte_perm(ab_hi, cd_hi, 0x5410);
         P[3] = __byte_perm(ab_hi, cd_hi, 0x7632);
+    }
+
+    template <int L, int SP>
+    __device__ __forceinline__ static void load_vec(const Elem *const *base, const int *res, int gl, int k, T *P)
+    {
+        const int4 a = reinterpret_cast<const int4 *>(base[0])[(res[0] * (SP / 16) + k) * L + gl];
+        const int4 b = reinterpret_cast<const int4 *>(base[1])[(res[1] * (SP / 16) + k) * L + gl];
+        const int4 c = reinterpret_cast<const int4 *>(base[2])[(res[2] * (SP / 16) + k) * L + gl];
+        const int4 d = reinterpret_cast<const int4 *>(base[3])[(res[3] * (SP / 16) + k) * L + gl];
+        transpose4(a.x, b.x, c.x, d.x, P + 0);
+        transpose4(a.y, b.y, c.y, d.y, P + 4);
+        transpose4(a.z, b.z, c.z, d.z, P + 8);
+        transpose4(a.w, b.w, c.w, d.w, P + 12);
     }
 
     template <int L, int S, int SP>

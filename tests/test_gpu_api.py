@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 ALL_PLANS = {
-    1: [(4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16)],
-    2: [(8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16)],
+    1: [(4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 32)],
+    2: [(8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24), (32, 32)],
     3: [(8, 16), (16, 16), (32, 16)],
 }
 
