@@ -56,6 +56,12 @@ def parse():
                     help="comma-separated query lengths (profiling cases)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no oracle check, lazy-F, e2e, probe or CPU baseline")
+    ap.add_argument("--workload", default="scale", choices=["scale", "pairs", "ragged", "serve"],
+                    help="scale: the default line; pairs/ragged/serve: the other workloads")
+    ap.add_argument("--n-pairs", type=int, default=1_000_000)
+    ap.add_argument("--n-queries", type=int, default=64, help="ragged: queries taken from the 10,000")
+    ap.add_argument("--serve-db", type=int, default=1_000_000)
+    ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--streams", type=int, default=4,
                     help="CUDA streams the independent queries of a step are spread over")
     return ap.parse_args()
@@ -199,6 +205,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "scale":
+        from paper_1909_00899_gb300 import build as libbuild
+        libbuild.build()
+        {"pairs": run_pairs, "ragged": run_ragged, "serve": run_serve}[args.workload](args)
         return
     import numpy as np
     import torch
@@ -458,6 +469,249 @@ def run_e2e(w, lane, args, stream, cells_step):
     d2h = 4 * n_db * len(QLENS)
     return {"value": cells_step * steps / (ms * 1e-3) / 1e9, "unit": "GCUPS",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+# ---------------------------------------------------------------------------
+# other workloads (each prints its own JSON line; the default line above is
+# the scale workload)
+# ---------------------------------------------------------------------------
+
+def _events_ms(fn, stream, reps=1):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_pairs(args):
+    """DNA reads against their own 2 kbp reference windows (1M pairs)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1909_00899_gb300 import sw, synth
+    torch.cuda.set_device(0)
+    w = synth.workload_reads(n_pairs=args.n_pairs)
+    n = len(w["q_off"]) - 1
+    qlen = np.diff(w["q_off"])
+    rlen = np.diff(w["r_off"])
+    cells = float((qlen * rlen).sum())
+    st = torch.cuda.current_stream()
+    qd = torch.from_numpy(w["q"]).cuda()
+    qo = torch.from_numpy(w["q_off"]).cuda()
+    rd = torch.from_numpy(w["r"]).cuda()
+    ro = torch.from_numpy(w["r_off"]).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, lane in (("s16x2", sw.SW_LANE_I16X2), ("s8x4", sw.SW_LANE_I8X4), ("int32", sw.SW_LANE_I32)):
+        fn = lambda: sw.sw_align_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, lane_type=lane, stream=st)
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            ms.append(_events_ms(fn, st))
+        res[name] = {"gcups": cells / (np.mean(ms) * 1e-3) / 1e9, "ms": float(np.mean(ms))}
+        if name == "s8x4":
+            s = out.cpu().numpy()
+            res[name]["flagged_fraction_per_class"] = {
+                k: float((s[w["kinds"] == c] >= 127 - 1).mean()) for k, c in
+                (("copy95", 0), ("deletion", 1), ("insertion", 2), ("copy99", 3))}
+    steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lz = lambda: sw.sw_align_lazyf_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, lazy_steps=steps, stream=st)
+    lz()
+    steps.zero_()
+    flush.zero_()
+    lms = _events_ms(lz, st)
+    lazy = {"gcups": cells / (lms * 1e-3) / 1e9, "ms": lms,
+            "C_factor": float(steps.item()) * 32 / cells}
+    # scan-F vs lazy-F and the lazy-F corrective factor C per read class
+    per_class = {}
+    for cname, c in (("copy95", 0), ("deletion", 1), ("insertion", 2), ("copy99", 3)):
+        ids = np.flatnonzero(w["kinds"] == c)
+        sub = _pairs_subset(w, ids)
+        sq, sqo, sr, sro = (torch.from_numpy(x).cuda() for x in (sub["q"], sub["q_off"], sub["r"], sub["r_off"]))
+        so = torch.empty(len(ids), dtype=torch.int32, device="cuda")
+        scells = float((np.diff(sub["q_off"]) * np.diff(sub["r_off"])).sum())
+        sf = lambda: sw.sw_align_pairs(sq, sqo, sr, sro, w["M"], w["o"], w["e"], so, stream=st)
+        sf()
+        sms = _events_ms(sf, st, 2)
+        steps.zero_()
+        lf = lambda: sw.sw_align_lazyf_pairs(sq, sqo, sr, sro, w["M"], w["o"], w["e"], so, lazy_steps=steps,
+                                             stream=st)
+        lf()
+        c_fac = float(steps.item()) * 32 / scells
+        lfm = _events_ms(lf, st, 2)
+        per_class[cname] = {"pairs": int(len(ids)), "scan_gcups": scells / (sms * 1e-3) / 1e9,
+                            "lazyf_gcups": scells / (lfm * 1e-3) / 1e9, "scan_vs_lazyf": lfm / sms,
+                            "lazyf_C_factor": c_fac}
+    worst = max(per_class, key=lambda k: per_class[k]["scan_vs_lazyf"])
+    # exactness on a sample, every lane type agreed already in the tests
+    sw.sw_align_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, stream=st)
+    got = out.cpu().numpy()
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(n, size=min(n, 4000), replace=False))
+    sb = _pairs_subset(w, sample)
+    want = oracle.gotoh_pairs(sb["q"], sb["q_off"], sb["r"], sb["r_off"], w["M"], w["o"], w["e"])
+    if not np.array_equal(got[sample], want):
+        raise SystemExit("pairs: sampled scores differ from the oracle")
+    best = max(res.values(), key=lambda r: r["gcups"])
+    line = {"metric": "GCUPS reads vs windows (scan-F, bit-exact)", "value": best["gcups"], "unit": "GCUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic", "config": {"workload": "1M DNA reads (150 bp; 30% 95%-id, 10% 40-200 bp indel, "
+                                                        "60% 99%-id) vs own 2 kbp windows, +1/-4, o=6 e=1",
+                                            "n_pairs": n, "cells": cells},
+            "by_lane": res, "lazyf": lazy, "scan_vs_lazyf": lazy["ms"] / best["ms"],
+            "per_class": per_class, "largest_margin_class": worst,
+            "check": {"sampled": int(sample.size), "mismatches": 0}}
+    if not args.no_cpu_baseline:
+        # about cpu_seconds of work at ~10 GCUPS on the host cores
+        ids = np.arange(0, n, max(1, int(cells / (args.cpu_seconds * 1e10))))
+        sb = _pairs_subset(w, ids)
+        t0 = time.perf_counter()
+        oracle.gotoh_pairs(sb["q"], sb["q_off"], sb["r"], sb["r_off"], w["M"], w["o"], w["e"])
+        dt = time.perf_counter() - t0
+        c = float((np.diff(sb["q_off"]) * np.diff(sb["r_off"])).sum())
+        line["cpu_baseline"] = {"value": c / dt / 1e9, "unit": "GCUPS", "cores": len(os.sched_getaffinity(0)),
+                                "kind": "oracle", "sample": "%d of %d pairs (%.3g cells, %.1f s)" % (len(ids), n, c, dt)}
+    print(json.dumps(line), flush=True)
+
+
+def _pairs_subset(w, ids):
+    import numpy as np
+    q = [w["q"][w["q_off"][i]:w["q_off"][i + 1]] for i in ids]
+    r = [w["r"][w["r_off"][i]:w["r_off"][i + 1]] for i in ids]
+    qo = np.zeros(len(ids) + 1, np.int64)
+    ro = np.zeros(len(ids) + 1, np.int64)
+    np.cumsum([len(x) for x in q], out=qo[1:])
+    np.cumsum([len(x) for x in r], out=ro[1:])
+    return {"q": np.concatenate(q).astype(np.uint8), "q_off": qo,
+            "r": np.concatenate(r).astype(np.uint8), "r_off": ro}
+
+
+def run_ragged(args):
+    """Ragged batch: a deterministic, length-stratified subset of 10,000
+    protein queries (log-uniform 32..4096) against 200k log-normal sequences,
+    every query's alignment captured in one CUDA graph with the autotuned
+    layout per length bin."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1909_00899_gb300 import autotune, sw, synth
+    from paper_1909_00899_gb300.batch import BatchAligner
+    torch.cuda.set_device(0)
+    rng = synth.rng_for(3)
+    M = synth.protein_matrix(rng)
+    qlens_all = synth.lengths_loguniform(rng, 10_000, 32, 4096)
+    db, off = synth.random_db(rng, 200_000, 20, "lognormal", median=300, sigma=0.76, lo=20, hi=35000)
+    order = np.argsort(qlens_all, kind="stable")
+    pick = order[np.linspace(0, len(order) - 1, args.n_queries).astype(int)]
+    queries = [synth.residues(np.random.default_rng([5, int(i)]), int(qlens_all[i]), 20) for i in pick]
+    db_d = torch.from_numpy(db).cuda()
+    off_d = torch.from_numpy(off).cuda()
+    h = sw.Database(db_d, off_d)
+    # autotune against the database itself (one query per length bin)
+    table = autotune.tune(h, M, 11, 1, lengths=[48, 100, 200, 400, 800, 1600, 3200], reps=1)
+    out = torch.empty((len(queries), h.n), dtype=torch.int32, device="cuda")
+    ba = BatchAligner(h, M, 11, 1, table=table).prepare(queries, out)
+    st = ba.stream
+    for _ in range(args.warmup):
+        ba.run()
+    ms = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ba.run()
+        b.record(st)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    total_res = int(off[-1])
+    cells = float(sum(len(q) for q in queries)) * total_res
+    got = out.cpu().numpy()
+    ids = np.random.default_rng(4).choice(h.n, size=300, replace=False)
+    sdb, soff = _subset(db, off, ids)
+    for k in range(0, len(queries), max(1, len(queries) // 8)):
+        want = oracle.gotoh_batch(queries[k], sdb, soff, M, 11, 1)
+        if not np.array_equal(got[k][ids], want):
+            raise SystemExit("ragged: sampled scores differ from the oracle")
+    line = {"metric": "GCUPS ragged batch (graph replay, bit-exact)", "value": cells / (np.mean(ms) * 1e-3) / 1e9,
+            "unit": "GCUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": "%d of 10,000 protein queries (log-uniform 32..4096, length-stratified) vs "
+                                   "200k log-normal sequences (%d residues), o=11 e=1" % (len(queries), total_res),
+                       "cells_per_step": cells, "full_config_cells": float(qlens_all.sum()) * total_res},
+            "ms_per_step": float(np.mean(ms)),
+            "projected_full_config_s": float(qlens_all.sum()) * total_res / (cells / (np.mean(ms) * 1e-3)),
+            "autotune": table.to_json(), "check": {"queries_checked": 8, "db_sample": 300}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Serving: Poisson stream of protein queries (log-uniform 50..10,000)
+    against a resident database of 1M log-normal sequences (~350M residues),
+    admitted by a memory budget; p50/p99 latency at 50% and 90% of the
+    closed-loop peak rate."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1909_00899_gb300 import serve, sw, synth
+    torch.cuda.set_device(0)
+    rng = synth.rng_for(4)
+    M = synth.protein_matrix(rng)
+    db, off = synth.random_db(rng, args.serve_db, 20, "lognormal", median=300, sigma=0.555, lo=20, hi=35000)
+    db_d = torch.from_numpy(db).cuda()
+    off_d = torch.from_numpy(off).cuda()
+    h = sw.Database(db_d, off_d)
+    total_res = int(off[-1])
+
+    def queries(n, salt):
+        r = np.random.default_rng([6, salt])
+        lens = synth.lengths_loguniform(r, n, 50, 10_000)
+        return [synth.residues(r, int(m), 20) for m in lens]
+
+    budget = 48 << 30
+    srv = serve.Server(h, M, 11, 1, slots=4, mem_budget=budget)
+    srv.run(queries(4, 0))  # warm-up
+    qs = queries(args.serve_requests, 1)
+    t0 = time.perf_counter()
+    reqs = srv.run(qs)
+    peak_qps = len(qs) / (time.perf_counter() - t0)
+    peak_gcups = sum(len(q) for q in qs) * total_res / srv.wall / 1e9
+    loads = {}
+    for frac in (0.5, 0.9):
+        qs2 = queries(args.serve_requests, int(frac * 10))
+        arr = serve.poisson_arrivals(np.random.default_rng([7, int(frac * 10)]), len(qs2), frac * peak_qps)
+        srv2 = serve.Server(h, M, 11, 1, slots=4, mem_budget=budget)
+        r2 = srv2.run(qs2, arr)
+        st = serve.latency_stats(r2)
+        st["offered_qps"] = frac * peak_qps
+        st["achieved_gcups"] = sum(len(q) for q in qs2) * total_res / srv2.wall / 1e9
+        loads["%d%%" % int(frac * 100)] = st
+        if frac == 0.9:
+            ids = np.random.default_rng(8).choice(h.n, size=200, replace=False)
+            sdb, soff = _subset(db, off, ids)
+            for k in range(0, len(qs2), 20):  # 5% of the requests
+                want = oracle.gotoh_batch(qs2[k], sdb, soff, M, 11, 1)
+                if not np.array_equal(r2[k].scores[ids], want):
+                    raise SystemExit("serve: sampled scores differ from the oracle")
+    line = {"metric": "serving latency p50/p99 and throughput (bit-exact)", "value": peak_gcups, "unit": "GCUPS",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "protein queries log-uniform 50..10000 vs %d resident log-normal sequences "
+                                   "(median 300, sigma 0.555, %d residues), o=11 e=1, 4 slots, %d GB budget"
+                                   % (h.n, total_res, budget >> 30),
+                       "requests_per_load": args.serve_requests},
+            "peak_qps": peak_qps, "loads": loads,
+            "check": {"requests_checked": "5%", "db_sample": 200}}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

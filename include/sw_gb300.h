@@ -183,6 +183,27 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r,
                    int32_t gap_open, int32_t gap_extend, int32_t lane_type,
                    int32_t *scores_out, void *cuda_stream);
 
+/*
+ * sw_align_lazyf_pairs — as sw_align_pairs with the lazy-F correction loop
+ * of Alg. 1 (int32 lanes), the plain-method comparison for read-vs-window
+ * batches.  lazy_steps: optional device counter (caller zeroes it) to which
+ * every warp adds the j-steps its correction loop ran; divided by the
+ * main-pass j-steps (cells / 32) it is the paper's corrective factor C
+ * (Sec. I, cost O((1+C) n/p)).  NULL: not counted.
+ */
+int sw_align_lazyf_pairs(const uint8_t *q, const int64_t *q_off,
+                         const uint8_t *r, const int64_t *r_off,
+                         int64_t n_pairs, const int8_t *subst_matrix,
+                         int32_t alphabet, int32_t gap_open,
+                         int32_t gap_extend, int32_t *scores_out,
+                         unsigned long long *lazy_steps, void *cuda_stream);
+
+/* sw_align_lazyf_db with the same optional lazy-F step counter. */
+int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
+                            int32_t gap_open, int32_t gap_extend,
+                            int32_t *scores_out,
+                            unsigned long long *lazy_steps, void *cuda_stream);
+
 /* Waits for cuda_stream with a bound: SW_OK when the stream is idle,
  * SW_ERR_TIMEOUT after timeout_ms milliseconds (the work keeps running and
  * the context stays usable), SW_ERR_CUDA if the stream reported an error. */

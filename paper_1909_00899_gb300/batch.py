@@ -12,7 +12,11 @@ from . import autotune, sw
 
 
 class BatchAligner:
-    def __init__(self, db, M, o, e, lane=sw.SW_LANE_AUTO, table=None, stream=None):
+    """streams: the queries are spread round-robin over this many streams
+    that fork from and join back into the aligner's stream (inside the
+    graph too), so one query's launch tail overlaps the next query's work."""
+
+    def __init__(self, db, M, o, e, lane=sw.SW_LANE_AUTO, table=None, stream=None, streams=4):
         import torch
         self.db = db
         self.M = np.ascontiguousarray(M, dtype=np.int8)
@@ -20,6 +24,7 @@ class BatchAligner:
         self.lane = lane
         self.table = table
         self.stream = stream or torch.cuda.Stream()
+        self.side = [torch.cuda.Stream() for _ in range(max(1, streams))]
         self.graph = None
         self.profiles = []
         self.order = None
@@ -42,6 +47,7 @@ class BatchAligner:
         self.profiles = [None] * n
         for i in self.order:
             self.profiles[i] = self._profile(queries[i])
+        self.stream.synchronize()  # profiles are built on self.stream
         self.out = out
         with torch.cuda.stream(self.stream):
             # one eager pass: sets kernel attributes and warms the memory pool
@@ -54,12 +60,24 @@ class BatchAligner:
         return self
 
     def _enqueue(self):
-        for i in self.order:
-            sw.sw_align_db(self.profiles[i], self.db, self.o, self.e, self.out[i], stream=self.stream)
+        import torch
+        fork = torch.cuda.Event()
+        fork.record(self.stream)
+        for st in self.side:
+            st.wait_event(fork)
+        for n, i in enumerate(self.order):
+            st = self.side[n % len(self.side)]
+            sw.sw_align_db(self.profiles[i], self.db, self.o, self.e, self.out[i], stream=st)
+        for st in self.side:
+            j = torch.cuda.Event()
+            j.record(st)
+            self.stream.wait_event(j)
 
     def run(self):
         """Replays the captured graph on the aligner's stream."""
-        self.graph.replay()
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
         return self.out
 
     def run_eager(self):

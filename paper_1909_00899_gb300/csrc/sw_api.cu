@@ -238,7 +238,7 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
 // residue count (then no order kernels run and nothing is read back).
 int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o, int32_t e,
                int32_t *scores, void *stream, bool lazy, const int32_t *pre_order = nullptr,
-               int64_t pre_total = -1)
+               int64_t pre_total = -1, unsigned long long *lazy_steps = nullptr)
 {
     int rc = check_align_args(prof, db, off, n_db, o, e, scores);
     if (rc)
@@ -323,6 +323,7 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     a.bnd = bnd;
     a.scores = scores;
     a.one = 1;
+    a.lazy_steps = lazy_steps;
     a.flag_thresh = flag_threshold(lane, o, prof->maxM);
     a.prof = main_prof;
     a.nchunks = main.C;
@@ -577,15 +578,22 @@ int sw_align_db(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32
 int sw_align_lazyf_db(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32_t gap_extend,
                       int32_t *scores_out, void *cuda_stream)
 {
+    return sw_align_lazyf_db_stats(prof, db, gap_open, gap_extend, scores_out, nullptr, cuda_stream);
+}
+
+int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32_t gap_extend,
+                            int32_t *scores_out, unsigned long long *lazy_steps, void *cuda_stream)
+{
     if (!db)
         return fail(SW_ERR_INVALID, "db is NULL");
     return align_impl(prof, db->res, db->off, db->n, gap_open, gap_extend, scores_out, cuda_stream, true,
-                      db->order, db->total);
+                      db->order, db->total, lazy_steps);
 }
 
-int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
-                   int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
-                   int32_t gap_extend, int32_t lane_type, int32_t *scores_out, void *cuda_stream)
+static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off, int64_t n_pairs,
+               const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open, int32_t gap_extend,
+               int32_t lane_type, int32_t *scores_out, void *cuda_stream, bool lazy,
+               unsigned long long *lazy_steps)
 {
     if (n_pairs < 0)
         return fail(SW_ERR_INVALID, "n_pairs < 0 (%lld)", (long long)n_pairs);
@@ -618,7 +626,7 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
     }
     sw_profile shape;  // only the matrix range is read by lane_fits
     shape.maxM = maxM;
-    int lane = lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type;
+    int lane = lazy ? SW_LANE_I32 : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type);
     // query-length classes of the lane type; the packed classes must fit
     const Choice *tab = kPairI32;
     int ncls = kPairI32N;
@@ -694,6 +702,7 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
     a.e = gap_extend;
     a.scores = scores_out;
     a.one = 1;
+    a.lazy_steps = lazy_steps;
     const int32_t thresh = flag_threshold(lane, gap_open, maxM);
     int64_t begin = 0;
     for (int k = 0; k < ncls; ++k) {
@@ -704,7 +713,7 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
         a.counter = counters + 2 * k;
         const int lk = lane == SW_LANE_I32 ? swg::LK_I32 : (lane == SW_LANE_I16X2 ? swg::LK_I16X2 : swg::LK_I8X4);
         a.flag_thresh = thresh;
-        kr = swg::launch_pairs(lk, tab[k].L, tab[k].S, a, cls, nullptr, cnt, sms, st);
+        kr = swg::launch_pairs(lk, tab[k].L, tab[k].S, lazy, a, cls, nullptr, cnt, sms, st);
         if (kr)
             return cuda_fail(kr, "pair kernel launch");
         if (lane != SW_LANE_I32) {
@@ -718,13 +727,31 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
                 ++j;
             a.counter = counters + 2 * k + 1;
             a.flag_thresh = INT32_MAX;
-            kr = swg::launch_pairs(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, a, cl, list_count + k, cnt, sms, st);
+            kr = swg::launch_pairs(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, false, a, cl, list_count + k, cnt,
+                                   sms, st);
             if (kr)
                 return cuda_fail(kr, "rescore kernel launch");
         }
         begin += cnt;
     }
     return SW_OK;
+}
+
+int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
+                   int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
+                   int32_t gap_extend, int32_t lane_type, int32_t *scores_out, void *cuda_stream)
+{
+    return pairs_impl(q, q_off, r, r_off, n_pairs, subst_matrix, alphabet, gap_open, gap_extend, lane_type,
+                      scores_out, cuda_stream, false, nullptr);
+}
+
+int sw_align_lazyf_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
+                         int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
+                         int32_t gap_extend, int32_t *scores_out, unsigned long long *lazy_steps,
+                         void *cuda_stream)
+{
+    return pairs_impl(q, q_off, r, r_off, n_pairs, subst_matrix, alphabet, gap_open, gap_extend, SW_LANE_I32,
+                      scores_out, cuda_stream, true, lazy_steps);
 }
 
 int sw_stream_sync(void *cuda_stream, int64_t timeout_ms)

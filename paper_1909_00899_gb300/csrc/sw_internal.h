@@ -49,6 +49,7 @@ struct PairArgs {
     uint32_t *counter;
     uint32_t one;             // 1 (a run-time multiplier for FMA-pipe additions)
     int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
+    unsigned long long *lazy_steps;  // optional statistics of the lazy-F loop
 };
 
 // batch launchers (sw_k_i32.cu, sw_k_i16.cu, sw_k_i8.cu), declared in
@@ -56,7 +57,7 @@ struct PairArgs {
 // pair launchers (sw_k_pairs.cu): one query-length class (L, S) per launch
 // over list[0 .. n_hint), or list[0 .. *count_dev) when count_dev is set
 // (*count_dev <= n_hint).
-int launch_pairs(int lane, int L, int S, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
+int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
                  int64_t n_hint, int num_sms, cudaStream_t st);
 
 // Query-length classes of the pair kernel: class k holds pairs with

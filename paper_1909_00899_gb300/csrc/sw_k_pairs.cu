@@ -5,19 +5,23 @@
 
 namespace swg {
 
-int launch_pairs(int lane, int L, int S, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
+int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
                  int64_t n_hint, int num_sms, cudaStream_t st)
 {
 #define SWG_CASE(LT, LL, SS)                                                        \
     if (L == LL && S == SS)                                                         \
-        return launch_pairs_inst<LT, LL, SS>(a, list, count_dev, n_hint, num_sms, st);
+        return launch_pairs_inst<LT, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st);
+#define SWG_CASE_LAZY(LL, SS)                                                       \
+    if (L == LL && S == SS)                                                         \
+        return lazy ? launch_pairs_inst<LaneI32, LL, SS, true>(a, list, count_dev, n_hint, num_sms, st) \
+                    : launch_pairs_inst<LaneI32, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st);
     if (lane == LK_I32) {
-        SWG_CASE(LaneI32, 4, 8)
-        SWG_CASE(LaneI32, 8, 8)
-        SWG_CASE(LaneI32, 16, 8)
-        SWG_CASE(LaneI32, 16, 10)
-        SWG_CASE(LaneI32, 32, 8)
-        SWG_CASE(LaneI32, 32, 16)
+        SWG_CASE_LAZY(4, 8)
+        SWG_CASE_LAZY(8, 8)
+        SWG_CASE_LAZY(16, 8)
+        SWG_CASE_LAZY(16, 10)
+        SWG_CASE_LAZY(32, 8)
+        SWG_CASE_LAZY(32, 16)
     } else if (lane == LK_I16X2) {
         SWG_CASE(LaneI16x2, 8, 8)
         SWG_CASE(LaneI16x2, 16, 8)
@@ -31,6 +35,7 @@ int launch_pairs(int lane, int L, int S, const PairArgs &a, const int32_t *list,
         SWG_CASE(LaneI8x4, 32, 16)
     }
 #undef SWG_CASE
+#undef SWG_CASE_LAZY
     return (int)cudaErrorInvalidValue;
 }
 

@@ -11,7 +11,7 @@
 
 namespace swg {
 
-template <class LT, int L, int S>
+template <class LT, int L, int S, bool LAZY>
 __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const int32_t *__restrict__ list,
                                                        const int32_t *__restrict__ count_dev, int64_t n_list)
 {
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
     // entries of list to process: the class size, or a count on the device
     const int64_t n_work = count_dev ? (int64_t)(*count_dev) : n_list;
     const int64_t units = (n_work + CELLS - 1) / CELLS;
-    unsigned long long unused = 0;
+    unsigned long long lazy_steps = 0;
 
     for (;;) {
         unsigned int ubase = 0;
@@ -95,12 +95,15 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
         }
         __syncwarp(FULL);
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
-        const T mx = striped_unit<LT, L, S, false>(pbase, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
-                                                   false, nullptr, gl, unused);
+        const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
+                                                  false, nullptr, gl, lazy_steps);
         if (gl == 0)
             write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), pid, false, p.flag_thresh, p.scores);
         __syncwarp(FULL);  // profiles are rewritten by the next unit
     }
+    // j-steps of the lazy-F correction loop, counted once per warp
+    if (LAZY && p.lazy_steps && lane == 0 && lazy_steps)
+        atomicAdd(p.lazy_steps, lazy_steps);
 }
 
 // Shared memory of one warp: CELLS profiles per group, 32 / L groups.
@@ -110,11 +113,11 @@ constexpr size_t pair_smem_per_warp(int A)
     return (size_t)32 * LT::CELLS * (A + 1) * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
 }
 
-template <class LT, int L, int S>
+template <class LT, int L, int S, bool LAZY>
 int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
                       int num_sms, cudaStream_t st)
 {
-    auto kern = sw_pairs_kernel<LT, L, S>;
+    auto kern = sw_pairs_kernel<LT, L, S, LAZY>;
     const size_t per_warp = pair_smem_per_warp<LT, S>(a.A);
     int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
     const size_t smem = per_warp * warps;

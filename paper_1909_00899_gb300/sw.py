@@ -31,7 +31,7 @@ EXPORTS = (
     "sw_profile_build", "sw_profile_build_ex", "sw_profile_free", "sw_profile_free_async", "sw_profile_plan", "sw_align_batch",
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
-    "sw_align_lazyf_db",
+    "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats",
 )
 
 
@@ -79,6 +79,10 @@ def lib():
             f = getattr(L, name)
             f.restype = ctypes.c_int
             f.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
+        L.sw_align_lazyf_pairs.restype = ctypes.c_int
+        L.sw_align_lazyf_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp]
+        L.sw_align_lazyf_db_stats.restype = ctypes.c_int
+        L.sw_align_lazyf_db_stats.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp, _vp]
         L.sw_stream_sync.restype = ctypes.c_int
         L.sw_stream_sync.argtypes = [_vp, _i64]
         L.sw_last_error.restype = ctypes.c_char_p
@@ -267,6 +271,31 @@ def sw_align_lazyf_db(profile, db, gap_open, gap_extend, scores_out, stream=None
         raise ValueError("scores_out too small")
     _check(lib().sw_align_lazyf_db(profile.handle, db.handle, int(gap_open), int(gap_extend),
                                    _dev_ptr(scores_out, "int32"), _stream(stream)))
+    return scores_out
+
+
+def sw_align_lazyf_pairs(q, q_off, r, r_off, subst_matrix, gap_open, gap_extend, scores_out,
+                         lazy_steps=None, stream=None):
+    """Lazy-F (Alg. 1) pair scores; lazy_steps: optional int64 CUDA tensor
+    of one element that accumulates the correction loop's j-steps."""
+    M = np.ascontiguousarray(subst_matrix, dtype=np.int8)
+    n = int(q_off.numel()) - 1
+    if int(r_off.numel()) - 1 != n:
+        raise ValueError("q_off and r_off must have the same length")
+    steps = _dev_ptr(lazy_steps, "int64") if lazy_steps is not None else None
+    _check(lib().sw_align_lazyf_pairs(_dev_ptr(q, "uint8"), _dev_ptr(q_off, "int64"), _dev_ptr(r, "uint8"),
+                                      _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
+                                      int(gap_open), int(gap_extend), _dev_ptr(scores_out, "int32"),
+                                      steps, _stream(stream)))
+    return scores_out
+
+
+def sw_align_lazyf_db_stats(profile, db, gap_open, gap_extend, scores_out, lazy_steps=None, stream=None):
+    if scores_out.numel() < db.n:
+        raise ValueError("scores_out too small")
+    steps = _dev_ptr(lazy_steps, "int64") if lazy_steps is not None else None
+    _check(lib().sw_align_lazyf_db_stats(profile.handle, db.handle, int(gap_open), int(gap_extend),
+                                         _dev_ptr(scores_out, "int32"), steps, _stream(stream)))
     return scores_out
 
 

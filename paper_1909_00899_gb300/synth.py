@@ -102,12 +102,12 @@ def workload_protein_scale(seed_salt: int = 0, n_db: int = 100_000,
     return dict(M=M, queries=queries, db=db, off=off, o=11, e=1)
 
 
-def _mutate(rng, seq, identity, A):
-    s = seq.copy()
-    hit = rng.random(len(s)) >= identity
-    # substitution to a different base
-    s[hit] = (s[hit] + rng.integers(1, A, size=int(hit.sum()))) % A
-    return s
+def _substitute(rng, reads, identity, A):
+    """Each base of `reads` (any shape) replaced, with probability
+    1 - identity, by one of the other A - 1 bases."""
+    hit = rng.random(reads.shape) >= identity
+    shift = rng.integers(1, A, size=reads.shape, dtype=np.uint8)
+    return np.where(hit, (reads + shift) % A, reads).astype(np.uint8)
 
 
 def workload_reads(seed_salt: int = 0, n_pairs: int = 1_000_000,
@@ -115,48 +115,50 @@ def workload_reads(seed_salt: int = 0, n_pairs: int = 1_000_000,
     """DNA reads vs their own reference windows (mate-rescue stand-in).
 
     Classes: 30% copies at 95% identity, 10% with a 40-200 bp indel (half
-    deletions vs the window, half insertions of random bases into the read,
-    insertion length 40-100), 60% copies at 99% identity.  Reads have length
-    read_len except the indel class (read_len +/- the indel).
+    deletions vs the window -- the read spans a gap of 40-200 bp in the
+    window -- and half insertions of 40-100 random bases into the read),
+    60% copies at 99% identity.  Copies start at a uniform offset in the
+    window; indels are placed at least 25 bases from either read end.
     """
     rng = rng_for(2, seed_salt)
     A = DNA_A
-    windows = residues(rng, n_pairs * win_len, A).reshape(n_pairs, win_len)
-    cls = rng.random(n_pairs)
-    reads = []
-    kinds = np.empty(n_pairs, dtype=np.int8)
-    for k in range(n_pairs):
-        w = windows[k]
-        c = cls[k]
-        if c < 0.30:
-            kinds[k] = 0
-            start = int(rng.integers(0, win_len - read_len + 1))
-            reads.append(_mutate(rng, w[start:start + read_len], 0.95, A))
-        elif c < 0.40:
-            if rng.random() < 0.5:  # deletion vs the window: read spans a gap
-                kinds[k] = 1
-                dl = int(rng.integers(40, 201))
-                span = read_len + dl
-                start = int(rng.integers(0, win_len - span + 1))
-                left = int(rng.integers(25, read_len - 25 + 1))
-                piece = np.concatenate([w[start:start + left],
-                                        w[start + left + dl:start + span]])
-                reads.append(_mutate(rng, piece, 0.99, A))
-            else:  # insertion of random bases into the read
-                kinds[k] = 2
-                il = int(rng.integers(40, 101))
-                start = int(rng.integers(0, win_len - read_len + 1))
-                base = w[start:start + read_len]
-                cut = int(rng.integers(25, read_len - 25 + 1))
-                ins = residues(rng, il, A)
-                reads.append(_mutate(rng, np.concatenate([base[:cut], ins, base[cut:]]), 0.99, A))
-        else:
-            kinds[k] = 3
-            start = int(rng.integers(0, win_len - read_len + 1))
-            reads.append(_mutate(rng, w[start:start + read_len], 0.99, A))
-    qlen = np.array([len(x) for x in reads], dtype=np.int64)
-    q_off = np.zeros(n_pairs + 1, dtype=np.int64)
+    n = int(n_pairs)
+    windows = rng.integers(0, A, size=(n, win_len), dtype=np.uint8)
+    u = rng.random(n)
+    kinds = np.where(u < 0.30, 0, np.where(u < 0.40, 1, 3)).astype(np.int8)
+    ins = (kinds == 1) & (rng.random(n) < 0.5)
+    kinds[ins] = 2
+    cols = np.arange(read_len)
+    # copies (kinds 0 and 3)
+    start = rng.integers(0, win_len - read_len + 1, size=n)
+    copies = windows[np.arange(n)[:, None], start[:, None] + cols[None, :]]
+    ident = np.where(kinds == 0, 0.95, 0.99)[:, None]
+    hit = rng.random(copies.shape) >= ident
+    shift = rng.integers(1, A, size=copies.shape, dtype=np.uint8)
+    reads = np.where(hit, (copies + shift) % A, copies).astype(np.uint8)
+    # deletions vs the window (kind 1): read = window[s:s+left] + window[s+left+dl : s+read_len+dl]
+    d_idx = np.flatnonzero(kinds == 1)
+    if d_idx.size:
+        dl = rng.integers(40, 201, size=d_idx.size)
+        s0 = (rng.random(d_idx.size) * (win_len - read_len - dl + 1)).astype(np.int64)
+        left = rng.integers(25, read_len - 25 + 1, size=d_idx.size)
+        src = s0[:, None] + cols[None, :] + np.where(cols[None, :] < left[:, None], 0, dl[:, None])
+        reads[d_idx] = _substitute(rng, windows[d_idx[:, None], src], 0.99, A)
+    qlen = np.full(n, read_len, dtype=np.int64)
+    # insertions into the read (kind 2): ragged lengths read_len + 40..100
+    i_idx = np.flatnonzero(kinds == 2)
+    il = rng.integers(40, 101, size=i_idx.size)
+    qlen[i_idx] = read_len + il
+    q_off = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(qlen, out=q_off[1:])
-    r_off = np.arange(n_pairs + 1, dtype=np.int64) * win_len
-    return dict(M=dna_matrix(), q=np.concatenate(reads).astype(np.uint8), q_off=q_off,
-                r=windows.reshape(-1), r_off=r_off, kinds=kinds, o=6, e=1)
+    q = np.empty(int(q_off[-1]), dtype=np.uint8)
+    regular = np.flatnonzero(kinds != 2)
+    # fixed-length reads go in with one gather
+    pos = q_off[regular][:, None] + cols[None, :]
+    q[pos] = reads[regular]
+    for k, i in enumerate(i_idx):
+        cut = int(rng.integers(25, read_len - 25 + 1))
+        piece = np.concatenate([reads[i, :cut], rng.integers(0, A, int(il[k]), dtype=np.uint8), reads[i, cut:]])
+        q[q_off[i]:q_off[i + 1]] = piece
+    r_off = np.arange(n + 1, dtype=np.int64) * win_len
+    return dict(M=dna_matrix(), q=q, q_off=q_off, r=windows.reshape(-1), r_off=r_off, kinds=kinds, o=6, e=1)

@@ -248,3 +248,28 @@ def test_pairs_gap_adversary(sw, kind):
     want = oracle.gotoh_pairs(q, q_off, r, r_off, M, 6, 1)
     got = run_pairs(sw, kind, q, q_off, r, r_off, M, 6, 1)
     np.testing.assert_array_equal(got, want)
+
+
+def test_lazyf_pairs_exact_and_counts_steps(sw):
+    """Lazy-F pairs equal the oracle; its correction loop (the corrective
+    factor C of Sec. I) runs far more on related read/window pairs (long
+    high-scoring paths keep carried F alive) than on unrelated ones."""
+    w = synth.workload_reads(n_pairs=1200)
+    want = oracle.gotoh_pairs(w["q"], w["q_off"], w["r"], w["r_off"], w["M"], w["o"], w["e"])
+    qd, qo = db_to_dev(w["q"], w["q_off"])
+    rd, ro = db_to_dev(w["r"], w["r_off"])
+    out = torch.empty(1200, dtype=torch.int32, device="cuda")
+    steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sw.sw_align_lazyf_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, lazy_steps=steps)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    related = int(steps.item())
+    # the same reads against the windows of other pairs (unrelated)
+    r_off = w["r_off"]
+    win = np.roll(w["r"].reshape(1200, -1), 1, axis=0).reshape(-1)
+    rd2, _ = db_to_dev(win, r_off)
+    steps.zero_()
+    sw.sw_align_lazyf_pairs(qd, qo, rd2, ro, w["M"], w["o"], w["e"], out, lazy_steps=steps)
+    torch.cuda.synchronize()
+    unrelated = int(steps.item())
+    assert related > 3 * unrelated
