@@ -204,6 +204,34 @@ int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
                             int32_t *scores_out,
                             unsigned long long *lazy_steps, void *cuda_stream);
 
+/*
+ * sw_align_batch_noalloc — sw_align_batch (same arguments, results and
+ * errors) for callers that cannot let a library allocate device memory, for
+ * example an application whose own allocator has reserved the device's
+ * memory, or a host framework that forbids its plug-ins to allocate.  This
+ * call allocates nothing: its scratch (work order, counters, overflow list,
+ * chunk boundary rows) lives in one fixed device array of
+ * SW_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  The paper has no counterpart; it is a deployment
+ * variant of the batch path.
+ *  - The profile still comes from sw_profile_build (which allocates), so
+ *    build profiles up front.
+ *  - A call whose scratch would exceed the array (about 8 bytes per
+ *    sequence, plus 8 bytes per residue for queries longer than one chunk)
+ *    returns SW_ERR_RANGE before launching anything.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race; serialise them.  Each call
+ *    clears the counters it needs on its stream.
+ *  - The first call on a device looks the array's address up
+ *    (cudaGetSymbolAddress) with that device current; make it before any
+ *    stream capture.
+ */
+#define SW_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sw_align_batch_noalloc(const sw_profile *prof, const uint8_t *db_residues,
+                           const int64_t *db_offsets, int64_t n_db,
+                           int32_t gap_open, int32_t gap_extend,
+                           int32_t *scores_out, void *cuda_stream);
+
 /* Waits for cuda_stream with a bound: SW_OK when the stream is idle,
  * SW_ERR_TIMEOUT after timeout_ms milliseconds (the work keeps running and
  * the context stays usable), SW_ERR_CUDA if the stream reported an error. */

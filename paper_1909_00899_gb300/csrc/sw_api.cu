@@ -23,20 +23,6 @@ int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_
 
 using swg::Plan;
 
-struct sw_profile {
-    int device = 0;
-    int32_t qlen = 0, A = 0, lane = 0;
-    Plan plan;    // plan of the requested lane type
-    Plan plan32;  // int32 plan: lazy-F and the rescore of flagged alignments
-    void *block = nullptr;        // one stream-ordered allocation for all parts
-    cudaStream_t stream = nullptr;  // stream the profile was built on
-    uint8_t *d_query = nullptr;
-    int8_t *d_M = nullptr;
-    int8_t *d_prof = nullptr;
-    int8_t *d_prof32 = nullptr;
-    int32_t maxM = 0, minM = 0;
-};
-
 struct sw_db {
     int device = 0;
     const uint8_t *res = nullptr;
@@ -356,6 +342,27 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
 }
 
 }  // namespace
+
+// Helpers shared with the other host translation units (sw_noalloc.cu).
+namespace swg {
+int api_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+int api_cuda_fail(int err, const char *what) { return cuda_fail(err, what); }
+int api_num_sms(int dev) { return num_sms_of(dev); }
+bool api_lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan &pl)
+{
+    return lane_fits(lane, pf, o, e, pl);
+}
+int32_t api_flag_threshold(int lane, int32_t o, int32_t maxM) { return flag_threshold(lane, o, maxM); }
+int api_check_align_args(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o,
+                         int32_t e, int32_t *scores)
+{
+    return check_align_args(prof, db, off, n_db, o, e, scores);
+}
+int api_launch_plan(const Plan &pl, bool lazy, const BatchArgs &a, int sms, cudaStream_t st)
+{
+    return launch_plan(pl, lazy, a, sms, st);
+}
+}  // namespace swg
 
 extern "C" {
 

@@ -85,6 +85,35 @@ int launch_length_order(const int64_t *off, int64_t n, int32_t *order, int32_t *
 int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32_t *list, int32_t *count,
                          cudaStream_t st, int num_sms);
 
+}  // namespace swg
+
+// A built query profile (opaque in the public header).
+struct sw_profile {
+    int device = 0;
+    int32_t qlen = 0, A = 0, lane = 0;
+    swg::Plan plan;    // plan of the requested lane type
+    swg::Plan plan32;  // int32 plan: lazy-F and the rescore of flagged alignments
+    void *block = nullptr;          // one stream-ordered allocation for all parts
+    cudaStream_t stream = nullptr;  // stream the profile was built on
+    uint8_t *d_query = nullptr;
+    int8_t *d_M = nullptr;
+    int8_t *d_prof = nullptr;
+    int8_t *d_prof32 = nullptr;
+    int32_t maxM = 0, minM = 0;
+};
+
+namespace swg {
+
+// Host helpers of sw_api.cu shared with other host translation units.
+int api_fail(int code, const char *msg);
+int api_cuda_fail(int err, const char *what);
+int api_num_sms(int dev);
+bool api_lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan &pl);
+int32_t api_flag_threshold(int lane, int32_t o, int32_t maxM);
+int api_check_align_args(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o,
+                         int32_t e, int32_t *scores);
+int api_launch_plan(const Plan &pl, bool lazy, const BatchArgs &a, int sms, cudaStream_t st);
+
 // Cell-rate probe of the plain pass for the roofline: 'op' selects the
 // lane type (0 int32, 1 s16x2, 2 s8x4); returns cells updated and ms.
 int run_int_peak(int op, int blocks, int threads, int iters, double *cells, float *ms, cudaStream_t st);

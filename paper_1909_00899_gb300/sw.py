@@ -31,7 +31,7 @@ EXPORTS = (
     "sw_profile_build", "sw_profile_build_ex", "sw_profile_free", "sw_profile_free_async", "sw_profile_plan", "sw_align_batch",
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
-    "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats",
+    "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
 )
 
 
@@ -65,7 +65,7 @@ def lib():
         L.sw_profile_free_async.argtypes = [_vp, _vp]
         L.sw_profile_plan.restype = ctypes.c_int
         L.sw_profile_plan.argtypes = [_vp] + [ctypes.POINTER(_i32)] * 4
-        for name in ("sw_align_batch", "sw_align_lazyf_batch"):
+        for name in ("sw_align_batch", "sw_align_lazyf_batch", "sw_align_batch_noalloc"):
             f = getattr(L, name)
             f.restype = ctypes.c_int
             f.argtypes = [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp]
@@ -203,6 +203,14 @@ def sw_align_batch(profile, db_residues, db_offsets, gap_open, gap_extend, score
 def sw_align_lazyf_batch(profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream=None):
     """Lazy-F (Alg. 1) scores, the plain-method comparison."""
     return _align(lib().sw_align_lazyf_batch, profile, db_residues, db_offsets, gap_open, gap_extend,
+                  scores_out, stream)
+
+
+def sw_align_batch_noalloc(profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream=None):
+    """sw_align_batch without device allocation: scratch comes from the
+    library's fixed device array (SW_NOALLOC_SCRATCH_BYTES); concurrent calls
+    must be serialised by the caller."""
+    return _align(lib().sw_align_batch_noalloc, profile, db_residues, db_offsets, gap_open, gap_extend,
                   scores_out, stream)
 
 
