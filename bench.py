@@ -213,9 +213,10 @@ def main():
         return
     import numpy as np
     import torch
+    import torch.distributed
 
     from paper_1909_00899_gb300 import build as libbuild
-    from paper_1909_00899_gb300 import sw, synth
+    from paper_1909_00899_gb300 import dist, sw, synth
 
     global QLENS
     QLENS = tuple(int(x) for x in args.qlens.split(","))
@@ -224,8 +225,7 @@ def main():
         args.no_lazyf = True
     rank, world, local = dist_env()
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+        torch.distributed.init_process_group("nccl")
     torch.cuda.set_device(local)
     libbuild.build()
     lane = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2,
@@ -286,9 +286,7 @@ def main():
         for _, a, b in keep:
             total_ms += a.elapsed_time(b)
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = dist.max_over_ranks(total_ms, device="cuda")
         return total_ms
 
     def per_query(lazy=False):
