@@ -32,9 +32,7 @@ QLENS = (128, 512, 2048, 5000)
 # capture summarised in profiles/sw_batch_kernel_s16x2_32x32_m2048_100k.md
 # (chunk 0 of an m=2048 query against this database).  Set to None whenever
 # the kernel changes, until it is captured again.
-NCU_TRAFFIC = {"bytes_per_launch": 48.676352e6 + 267.91296e6,
-               "kernel": "sw_batch_kernel<LaneI16x2, 32, 32>", "launch": "m=2048 chunk 0 vs 100k sequences",
-               "source": "profiles/sw_batch_kernel_s16x2_32x32_m2048_100k.md"}
+NCU_TRAFFIC = None
 METRIC = "GCUPS scan-F (bit-exact) vs lazy-F"
 WORKLOAD = ("protein queries m in {128,512,2048,5000} vs 100k db seqs, log-normal lengths "
             "(median 300, sigma 0.76, clip [20,35000]), o=11 e=1")
@@ -46,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--lane", default="auto", choices=["auto", "i32", "i16x2", "i8x4"])
+    ap.add_argument("--lane", default="auto", choices=["auto", "i32", "i16x2", "i16x2q", "i8x4"])
     ap.add_argument("--n-db", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lazyf", action="store_true")
@@ -229,7 +227,7 @@ def main():
     torch.cuda.set_device(local)
     libbuild.build()
     lane = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2,
-            "i8x4": sw.SW_LANE_I8X4}[args.lane]
+            "i16x2q": sw.SW_LANE_I16X2Q, "i8x4": sw.SW_LANE_I8X4}[args.lane]
 
     w = synth.workload_protein_scale(n_db=args.n_db, qlens=QLENS)
     M, o, e = w["M"], w["o"], w["e"]
@@ -346,7 +344,7 @@ def main():
         # chunk, then for packed lanes the flag kernel and the int32 rescore
         launches_per_step += (2 if packed else 1) + 3 + pl["chunks"] + ((1 + pl32["chunks"]) if packed else 0)
     plan = plans[-1]
-    cells_per_op = {1: 1, 2: 2, 3: 4}[plan["lane_type"]]
+    cells_per_op = {1: 1, 2: 2, 3: 4, 4: 2}[plan["lane_type"]]
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     # integer ALU pipe: 16 lanes/clk per SM sub-partition, 4 per SM

@@ -50,10 +50,14 @@ extern "C" {
 #define SW_ERR_RANGE (-5)    /* matrix/gap values do not fit the lane type  */
 
 /* lane types: how many cells one 32-bit register carries */
-#define SW_LANE_AUTO 0   /* library picks (packed lanes + exact rescore)   */
+#define SW_LANE_AUTO 0   /* library picks lane type and layout per query
+                            length (packed lanes + exact rescore)         */
 #define SW_LANE_I32 1    /* one int32 cell per register                    */
 #define SW_LANE_I16X2 2  /* two int16 cells per register, DPX s16x2 ops    */
 #define SW_LANE_I8X4 3   /* four int8 cells per register, saturating SIMD  */
+#define SW_LANE_I16X2Q 4 /* two int16 cells per register: the two halves of
+                            one alignment's query (no byte permutes);
+                            plans count virtual lanes, two per thread     */
 
 typedef struct sw_profile sw_profile; /* opaque, owned by the library */
 
@@ -87,7 +91,8 @@ int sw_profile_build(const uint8_t *query, int32_t qlen,
  * shapes the kernels are compiled for are accepted (SW_ERR_INVALID
  * otherwise): int32 {4x8, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16,
  * 16x32, 32x32}, s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
- * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}.  Used by the autotuner.
+ * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}, split s16x2 (virtual lanes)
+ * {16x8, 32x8, 64x8, 64x16, 64x32}.  Used by the autotuner.
  */
 int sw_profile_build_ex(const uint8_t *query, int32_t qlen,
                         const int8_t *subst_matrix, int32_t alphabet,
@@ -245,7 +250,8 @@ const char *sw_last_error(void);
  * thread of a full-device grid updates independent cells with exactly the
  * per-cell instruction sequence of the scan-F pass (no loads, no
  * shuffles, no scan).  Writes cells per second (host double) for the lane
- * type (SW_LANE_I32, _I16X2 or _I8X4).  Synchronises cuda_stream.  Used as
+ * type (SW_LANE_I32, _I16X2, _I8X4, or _I16X2Q which runs the s16x2
+ * sequence).  Synchronises cuda_stream.  Used as
  * the measured denominator of the integer roofline.
  */
 int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_second,

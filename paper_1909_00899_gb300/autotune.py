@@ -21,6 +21,8 @@ CANDIDATES = {
     sw.SW_LANE_I16X2: ((8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24),
                        (32, 32)),
     sw.SW_LANE_I32: ((4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 32)),
+    # split-query s16x2: virtual lanes (two per thread)
+    sw.SW_LANE_I16X2Q: ((16, 8), (32, 8), (64, 8), (64, 16), (64, 32)),
 }
 
 
@@ -92,7 +94,7 @@ def _time_layout(db, query, M, o, e, lane, L, S, out, reps, stream):
         prof.free()
 
 
-def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I32), reps=2, seed=0,
+def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I16X2Q, sw.SW_LANE_I32), reps=2, seed=0,
          device_name=None, verbose=False):
     """Times every candidate layout for one query per length bin against the
     resident database `db` and returns the best per bin."""

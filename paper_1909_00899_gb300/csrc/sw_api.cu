@@ -19,6 +19,7 @@ namespace swg {
 int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_q16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 }  // namespace swg
 
 using swg::Plan;
@@ -96,6 +97,8 @@ struct Choice {
 const Choice kI32[] = {{4, 8}, {8, 8}, {16, 8}, {32, 8}, {32, 16}, {32, 32}};
 const Choice kI16[] = {{8, 8}, {16, 8}, {32, 8}, {32, 16}, {32, 32}};
 const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
+// split-query s16x2: virtual lanes (two per thread)
+const Choice kQ16[] = {{16, 8}, {32, 8}, {64, 8}, {64, 16}, {64, 32}};
 // every (lanes, segment length) the batch kernels are instantiated for
 const Choice kAllI32[] = {{4, 8}, {8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
@@ -103,8 +106,8 @@ const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
 
 bool plan_supported(int lane, int L, int S)
 {
-    const Choice *t = lane == SW_LANE_I32 ? kAllI32 : (lane == SW_LANE_I16X2 ? kAllI16 : kAllI8);
-    const int n = lane == SW_LANE_I32 ? 10 : (lane == SW_LANE_I16X2 ? 10 : 3);
+    const Choice *t = lane == SW_LANE_I32 ? kAllI32 : (lane == SW_LANE_I16X2 ? kAllI16 : lane == SW_LANE_I8X4 ? kAllI8 : kQ16);
+    const int n = lane == SW_LANE_I32 ? 10 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 5);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;
@@ -117,6 +120,39 @@ const Choice kPairI16[] = {{8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
 const Choice kPairI8[] = {{8, 16}, {16, 10}, {16, 16}, {32, 16}};
 const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4;
 
+// Automatic choice of lane type and layout: the layout maximising
+// (useful positions / chunk positions) x its measured rate on GB300
+// (GCUPS, 100k log-normal protein sequences; refined per workload by the
+// autotuner).
+struct AutoChoice {
+    int lane, L, S;
+    double gcups;
+};
+const AutoChoice kAuto[] = {
+    {SW_LANE_I16X2, 8, 8, 1400},    {SW_LANE_I16X2Q, 16, 8, 1900},  {SW_LANE_I16X2Q, 32, 8, 3000},
+    {SW_LANE_I16X2, 32, 16, 3670},  {SW_LANE_I16X2Q, 64, 8, 3370},  {SW_LANE_I16X2Q, 64, 16, 4100},
+    {SW_LANE_I16X2, 32, 32, 3870},  {SW_LANE_I16X2Q, 64, 32, 4350},
+};
+
+Plan choose_auto(int32_t qlen)
+{
+    Plan best;
+    double best_rate = -1.0;
+    for (const AutoChoice &c : kAuto) {
+        const int QC = c.L * c.S;
+        const int C = qlen > 0 ? (qlen + QC - 1) / QC : 1;
+        const double rate = c.gcups * (double)std::max(qlen, 1) / ((double)C * QC);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best.lane = c.lane;
+            best.L = c.L;
+            best.S = c.S;
+            best.C = qlen > 0 ? C : 0;
+        }
+    }
+    return best;
+}
+
 Plan choose_plan(int32_t qlen, int lane)
 {
     const Choice *tab = kI32;
@@ -127,6 +163,9 @@ Plan choose_plan(int32_t qlen, int lane)
     } else if (lane == SW_LANE_I8X4) {
         tab = kI8;
         n = 3;
+    } else if (lane == SW_LANE_I16X2Q) {
+        tab = kQ16;
+        n = 5;
     }
     Plan p;
     p.lane = lane;
@@ -145,17 +184,18 @@ bool lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan 
 {
     if (lane == SW_LANE_I32)
         return true;
-    const int64_t ceil = lane == SW_LANE_I16X2 ? 32767 : 127;
+    const int64_t ceil = lane == SW_LANE_I8X4 ? 127 : 32767;
     if (lane == SW_LANE_I8X4 && (int64_t)pf->maxM + o > ceil)
         return false;
     if (o > 127)
         return false;
-    if (lane == SW_LANE_I16X2) {
+    if (lane == SW_LANE_I16X2 || lane == SW_LANE_I16X2Q) {
         // biased halves stay positive: 2o + S*e below the X-space bias (4096),
-        // the deepest scan hop above -32768
+        // the deepest scan hop (and the split lane's fold of the first half,
+        // up to L*S*e over its L = plan lanes / 2 threads) above -32768
         if (2LL * o + (int64_t)pl.S * e + 256 > 4096)
             return false;
-        if (4096LL - o - (int64_t)(pl.L / 2) * pl.S * e < -32000)
+        if (4096LL - o - (int64_t)pl.L * pl.S * e < -32000)
             return false;
     } else {
         // the last-position correction subtracts (S-1)*e in one saturating add
@@ -170,7 +210,7 @@ bool lane_fits(int lane, const sw_profile *pf, int32_t o, int32_t e, const Plan 
 int32_t flag_threshold(int lane, int32_t o, int32_t maxM)
 {
     const int32_t m = std::max(maxM, 0);
-    if (lane == SW_LANE_I16X2)
+    if (lane == SW_LANE_I16X2 || lane == SW_LANE_I16X2Q)
         return 32767 - (4096 + 128 - o) - m;  // s16x2: h-space bias 4096 + 128 - o
     if (lane == SW_LANE_I8X4)
         return 127 - m;
@@ -217,6 +257,8 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
         return swg::launch_batch_i32(pl, lazy, a, sms, st);
     if (pl.lane == SW_LANE_I16X2)
         return swg::launch_batch_i16(pl, a, sms, st);
+    if (pl.lane == SW_LANE_I16X2Q)
+        return swg::launch_batch_q16(pl, a, sms, st);
     return swg::launch_batch_i8(pl, a, sms, st);
 }
 
@@ -390,7 +432,7 @@ int sw_profile_build_ex(const uint8_t *query, int32_t qlen, const int8_t *subst_
         return fail(SW_ERR_INVALID, "alphabet must be in 1..32 (got %d)", alphabet);
     if (!subst_matrix)
         return fail(SW_ERR_INVALID, "subst_matrix is NULL");
-    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I8X4)
+    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I16X2Q)
         return fail(SW_ERR_INVALID, "unknown lane_type %d", lane_type);
     for (int32_t i = 0; i < qlen; ++i)
         if (query[i] >= alphabet)
@@ -405,13 +447,15 @@ int sw_profile_build_ex(const uint8_t *query, int32_t qlen, const int8_t *subst_
         pf->maxM = std::max<int32_t>(pf->maxM, subst_matrix[i]);
         pf->minM = std::min<int32_t>(pf->minM, subst_matrix[i]);
     }
-    int lane = lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type;
+    int lane = lane_type;
+    if (lane_type == SW_LANE_AUTO)
+        lane = lanes ? SW_LANE_I16X2 : choose_auto(qlen).lane;
     if ((lanes == 0) != (seg_len == 0) || (lanes && !plan_supported(lane, lanes, seg_len))) {
         delete pf;
         return fail(SW_ERR_INVALID, "no kernel for lane type %d with %d lanes x %d positions", lane, lanes, seg_len);
     }
     pf->lane = lane;
-    pf->plan = choose_plan(qlen, lane);
+    pf->plan = lane_type == SW_LANE_AUTO && !lanes ? choose_auto(qlen) : choose_plan(qlen, lane);
     if (lanes) {
         pf->plan.L = lanes;
         pf->plan.S = seg_len;
@@ -613,7 +657,7 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
     if (alphabet < 1 || alphabet > 32)
         return fail(SW_ERR_INVALID, "alphabet must be in 1..32 (got %d)", alphabet);
     if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I8X4)
-        return fail(SW_ERR_INVALID, "unknown lane_type %d", lane_type);
+        return fail(SW_ERR_INVALID, "pairs take lane types AUTO, I32, I16X2 or I8X4 (got %d)", lane_type);
     if (gap_open < 1)
         return fail(SW_ERR_INVALID, "gap_open must be >= 1 (got %d)", gap_open);
     if (gap_extend < 0 || gap_extend > gap_open)
@@ -783,8 +827,10 @@ int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_secon
 {
     if (!cells_per_second)
         return fail(SW_ERR_INVALID, "cells_per_second is NULL");
-    if (lane_type < SW_LANE_I32 || lane_type > SW_LANE_I8X4)
-        return fail(SW_ERR_INVALID, "lane_type must be I32, I16X2 or I8X4");
+    if (lane_type < SW_LANE_I32 || lane_type > SW_LANE_I16X2Q)
+        return fail(SW_ERR_INVALID, "lane_type must be I32, I16X2, I8X4 or I16X2Q");
+    if (lane_type == SW_LANE_I16X2Q)
+        lane_type = SW_LANE_I16X2;  // the same cell sequence on the same lane type
     if (iters < 1)
         return fail(SW_ERR_INVALID, "iters must be >= 1");
     int dev = 0;

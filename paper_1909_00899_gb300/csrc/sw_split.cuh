@@ -1,0 +1,240 @@
+// Split-query s16x2 batch kernel: both 16-bit halves of a register belong to
+// the same alignment.  A chunk of the query has 2*L*S positions; lane l,
+// segment index j holds position l*S + j of the first half in its low half
+// and position L*S + l*S + j of the second half in its high half, i.e. the
+// striped layout of Alg. 1 over 2L virtual lanes (virtual lane L + l lives
+// in the high half of lane l).  The profile is packed per residue in shared
+// memory, so a 16-byte load brings four positions of both halves with no
+// byte permutes, and one residue per column is broadcast.
+//
+// Differences from the two-alignment s16x2 kernel (sw_batch.cuh):
+//  - the diagonal of lane 0's high half is lane L-1's last low-half value
+//    (position L*S - 1 precedes L*S);
+//  - after the log2 L scan of both halves at once, the F leaving the first
+//    half (the low half of lane L-1) is folded into the high halves with
+//    weight (l+1)*S*e, and it is the carry into the high half of lane 0.
+// Values use the biased X-space / h-space of LaneI16x2 (sw_lanes.cuh).
+#pragma once
+#include "sw_batch.cuh"
+
+namespace swg {
+
+struct LaneQ16 : LaneI16x2 {
+    using Elem = uint32_t;              // staged profile: (low position, high position) pair
+    static constexpr int CELLS = 1;     // one alignment per register
+    static constexpr int VEC = 4;       // staged pairs per 16 bytes
+    static constexpr bool CROSS = false;
+
+    template <int L, int SP>
+    __device__ __forceinline__ static void load_vec(const Elem *const *base, const int *res, int gl, int k, T *P)
+    {
+        const int4 v = reinterpret_cast<const int4 *>(base[0])[(res[0] * (SP / 4) + k) * L + gl];
+        P[0] = (uint32_t)v.x;
+        P[1] = (uint32_t)v.y;
+        P[2] = (uint32_t)v.z;
+        P[3] = (uint32_t)v.w;
+    }
+    // the alignment's maximum: both halves
+    __device__ __forceinline__ static int score(T mx, int, const K &k)
+    {
+        return max((int)(int16_t)(mx & 0xffffu), (int)(int16_t)(mx >> 16)) - k.bh;
+    }
+};
+
+// (lo of a, lo of b) -> (a.lo, b.lo)
+__device__ __forceinline__ uint32_t lo_lo(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5410); }
+
+template <int L, int S>
+// len: this group's reference length; ncols: the warp's longest (every
+// lane runs ncols columns, columns past len use the inert residue)
+__device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8_t *ref, int64_t start, int len,
+                                               int ncols, int A, int o, int e, uint32_t one, bool has_prev,
+                                               bool has_next, int2 *bnd, int gl)
+{
+    using LT = LaneQ16;
+    using T = uint32_t;
+    constexpr int SP = SegPad<S, 4>::value;
+    constexpr int LOGL = L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : L == 16 ? 4 : 5;
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int V = 4;
+
+    const LT::K k = LT::consts(o, e, S, one);
+    T negW[LOGL];
+#pragma unroll
+    for (int i = 0; i < LOGL; ++i)
+        negW[i] = LT::splat(-(1 << i) * S * e);
+    // fold of the first half's outgoing F into the second half: weight
+    // (l+1)*S*e on the high half only
+    const T wfold = (uint32_t)((-(gl + 1) * S * e) & 0xffff) << 16;
+    const T neg_lo = 0x00008000u;  // low half -32768, never wins a max
+    const uint32_t *pbase[1] = {prof};
+
+    T X[S], E[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        X[j] = k.xinit;
+        E[j] = k.hzero;
+    }
+    T c_prev = k.xzero;
+    T hlast = k.xinit;
+    T hb_lo = k.xinit;  // previous chunk's last X at the previous column (low half used)
+    T mx = k.hzero;
+
+    for (int r0 = 0; r0 < ncols; r0 += L) {
+        const int r = r0 + gl;
+        const int myres = r < len ? min((int)ref[start + r], A) : A;
+        int2 mybnd = make_int2(-o, 0);
+        if (has_prev && r < len)
+            mybnd = bnd[start + r];
+        const int cols = min(L, ncols - r0);
+        for (int rr = 0; rr < cols; ++rr) {
+            const int rc = r0 + rr;
+            int res[1];
+            res[0] = __shfl_sync(FULL, myres, rr, L);
+            T Pv[V];
+
+            // diagonal: lane l-1's last values; lane 0 takes the chunk
+            // boundary (low) and lane L-1's last low half (high)
+            const T up = __shfl_up_sync(FULL, hlast, 1, L);
+            const T last = __shfl_sync(FULL, hlast, L - 1, L);
+            T hd = up;
+            T F = k.xzero;
+            T lo_in = k.xinit;
+            if (has_prev) {
+                const int bh = __shfl_sync(FULL, mybnd.x, rr, L);
+                const int bf = __shfl_sync(FULL, mybnd.y, rr, L);
+                lo_in = hb_lo;
+                hb_lo = (uint32_t)((bh + LT::BX) & 0xffff) * 0x10001u;
+                if (gl == 0)
+                    F = lo_lo((uint32_t)((bf + LT::BX) & 0xffff), k.xzero);
+            }
+            if (gl == 0)
+                hd = lo_lo(lo_in, last);
+
+            T hpair = k.hzero;
+            if (__any_sync(FULL, LT::carry_pos(c_prev, k))) {
+                T d = LT::d0_of(c_prev, k);
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    if (j % V == 0)
+                        LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
+                    const T Ej = LT::max2(E[j], d);
+                    const T h = LT::h_of(hd, Pv[j % V], Ej, k);
+                    hd = LT::xd_corr(X[j], d, k);
+                    d = LT::dstep(d, k);
+                    const T ho = LT::ho_of(h, k);
+                    X[j] = LT::addmax(F, k.negO, ho);
+                    E[j] = LT::e_next(Ej, X[j], k);
+                    F = LT::addmax(F, k.negE, ho);
+                    if (j & 1)
+                        mx = LT::max3(mx, hpair, h);
+                    else if (j == S - 1)
+                        mx = LT::max2(mx, h);
+                    else
+                        hpair = h;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    if (j % V == 0)
+                        LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
+                    const T h = LT::h_of(hd, Pv[j % V], E[j], k);
+                    hd = X[j];
+                    const T ho = LT::ho_of(h, k);
+                    X[j] = LT::addmax(F, k.negO, ho);
+                    E[j] = LT::e_next(E[j], X[j], k);
+                    F = LT::addmax(F, k.negE, ho);
+                    if (j & 1)
+                        mx = LT::max3(mx, hpair, h);
+                    else if (j == S - 1)
+                        mx = LT::max2(mx, h);
+                    else
+                        hpair = h;
+                }
+            }
+            // scan of both halves at once, then the first half's outgoing F
+            // (low half of lane L-1) folded into the second half
+            T x = F;
+#pragma unroll
+            for (int i = 0; i < LOGL; ++i) {
+                const T y = __shfl_up_sync(FULL, x, 1 << i, L);
+                x = LT::addmax(y, negW[i], x);
+            }
+            const T gb = __shfl_sync(FULL, x, L - 1, L);
+            x = LT::addmax(lo_lo(neg_lo, gb), wfold, x);
+            T cin = __shfl_up_sync(FULL, x, 1, L);
+            if (gl == 0)
+                cin = lo_lo(k.xzero, gb);
+            c_prev = cin;
+            hlast = LT::last_corr(X[S - 1], cin, k);
+            if (has_next && gl == L - 1 && rc < len)
+                bnd[start + rc] = make_int2(LT::x_true(hlast, 1), LT::x_true(x, 1));
+        }
+    }
+#pragma unroll
+    for (int dd = L / 2; dd >= 1; dd >>= 1)
+        mx = LT::max2(mx, __shfl_xor_sync(FULL, mx, dd, L));
+    return mx;
+}
+
+template <int L, int S>
+__global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs p)
+{
+    constexpr int G = 32 / L;
+    constexpr int SP = SegPad<S, 4>::value;
+    constexpr int QH = L * S;  // positions per half
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sprof = reinterpret_cast<uint32_t *>(smem_raw);
+
+    // stage the chunk: raw profile of 2L virtual lanes [A][2L][S]; pair
+    // virtual lanes l and L + l into one 32-bit element
+    const int8_t *gprof = p.prof + (size_t)p.chunk * p.A * 2 * QH;
+    const int qbase = p.chunk * 2 * QH;
+    const int total = (p.A + 1) * L * SP;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int a = idx / (L * SP);
+        const int rem = idx - a * (L * SP);
+        const int l = rem / SP;
+        const int j = rem - l * SP;
+        int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
+        if (a < p.A && j < S) {
+            const int plo = l * S + j, phi = QH + l * S + j;
+            if (qbase + plo < p.qlen)
+                lo = (int)gprof[(size_t)a * 2 * QH + plo] + LaneQ16::PB;
+            if (qbase + phi < p.qlen)
+                hi = (int)gprof[(size_t)a * 2 * QH + phi] + LaneQ16::PB;
+        }
+        sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] = (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const int64_t n_work = p.n_work_dev ? (int64_t)(*p.n_work_dev) : p.n_work;
+    const bool has_prev = p.chunk > 0;
+    const bool has_next = p.chunk + 1 < p.nchunks;
+    const LaneQ16::K k = LaneQ16::consts(p.o, p.e, S, p.one);
+
+    for (;;) {
+        unsigned int ubase = 0;
+        if (lane == 0)
+            ubase = atomicAdd(p.counter, (unsigned int)G);
+        ubase = __shfl_sync(FULL, ubase, 0);
+        if ((int64_t)ubase >= n_work)
+            break;
+        const int64_t w = (int64_t)ubase + grp;
+        int seq[1];
+        seq[0] = w < n_work ? (p.order ? p.order[w] : (int)w) : -1;
+        const int64_t start = seq[0] >= 0 ? p.off[seq[0]] : 0;
+        const int len = seq[0] >= 0 ? (int)(p.off[seq[0] + 1] - start) : 0;
+        const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
+        const uint32_t mx = split_unit<L, S>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one, has_prev,
+                                             has_next, p.bnd, gl);
+        if (gl == 0)
+            write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);
+    }
+}
+
+}  // namespace swg

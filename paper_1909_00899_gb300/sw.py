@@ -25,6 +25,7 @@ SW_LANE_AUTO = 0
 SW_LANE_I32 = 1
 SW_LANE_I16X2 = 2
 SW_LANE_I8X4 = 3
+SW_LANE_I16X2Q = 4
 
 # every function declared in include/sw_gb300.h
 EXPORTS = (

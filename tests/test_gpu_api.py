@@ -18,6 +18,7 @@ ALL_PLANS = {
     1: [(4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 32)],
     2: [(8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24), (32, 32)],
     3: [(8, 16), (16, 16), (32, 16)],
+    4: [(16, 8), (32, 8), (64, 8), (64, 16), (64, 32)],
 }
 
 
@@ -62,7 +63,7 @@ def test_db_handle_matches_batch_and_oracle(sw, small_db):
     h.free()
 
 
-@pytest.mark.parametrize("lane", [1, 2, 3])
+@pytest.mark.parametrize("lane", [1, 2, 3, 4])
 def test_every_compiled_layout_is_exact(sw, small_db, lane):
     M, db, off = small_db["M"], small_db["db"], small_db["off"]
     db_d, off_d = db_to_dev(db[: off[120]], off[:121])

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-LANES = ["i32", "i16x2", "i8x4", "auto", "lazyf"]
+LANES = ["i32", "i16x2", "i16x2q", "i8x4", "auto", "lazyf"]
 
 
 @pytest.fixture(scope="module")
@@ -25,8 +25,8 @@ def sw():
 
 
 def run(sw, kind, query, M, db_d, off_d, o, e):
-    lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i8x4": sw.SW_LANE_I8X4,
-            "auto": sw.SW_LANE_AUTO, "lazyf": sw.SW_LANE_I32}[kind]
+    lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i16x2q": sw.SW_LANE_I16X2Q,
+            "i8x4": sw.SW_LANE_I8X4, "auto": sw.SW_LANE_AUTO, "lazyf": sw.SW_LANE_I32}[kind]
     prof = sw.Profile(query, M, lane)
     n = off_d.numel() - 1
     out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
@@ -114,7 +114,7 @@ def test_overflow_boundaries_rescored_exactly(sw, kind):
     np.testing.assert_array_equal(got, want)
 
 
-@pytest.mark.parametrize("kind", ["i16x2", "auto"])
+@pytest.mark.parametrize("kind", ["i16x2", "i16x2q", "auto"])
 def test_int16_ceiling(sw, kind):
     """True scores around 32767 - max(M) and above 32767 (identical
     sequences with a +11 diagonal) are rescored exactly."""
