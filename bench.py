@@ -56,7 +56,7 @@ def parse():
                     help="comma-separated query lengths (profiling cases)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no oracle check, lazy-F, e2e, probe or CPU baseline")
-    ap.add_argument("--workload", default="scale", choices=["scale", "pairs", "ragged", "serve"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "pairs", "ragged", "serve", "width"],
                     help="scale: the default line; pairs/ragged/serve: the other workloads")
     ap.add_argument("--n-pairs", type=int, default=1_000_000)
     ap.add_argument("--n-queries", type=int, default=64, help="ragged: queries taken from the 10,000")
@@ -209,7 +209,7 @@ def main():
     if args.workload != "scale":
         from paper_1909_00899_gb300 import build as libbuild
         libbuild.build()
-        {"pairs": run_pairs, "ragged": run_ragged, "serve": run_serve}[args.workload](args)
+        {"pairs": run_pairs, "ragged": run_ragged, "serve": run_serve, "width": run_width}[args.workload](args)
         return
     import numpy as np
     import torch
@@ -579,6 +579,54 @@ def run_pairs(args):
         line["cpu_baseline"] = {"value": c / dt / 1e9, "unit": "GCUPS", "cores": len(os.sched_getaffinity(0)),
                                 "kind": "oracle", "sample": "%d of %d pairs (%.3g cells, %.1f s)" % (len(ids), n, c, dt)}
     print(json.dumps(line), flush=True)
+
+
+def run_width(args):
+    """Lazy-F against the vector width (the GPU analogue of Fig. 1): int32
+    lanes, fixed query lengths, lanes per alignment L = 8, 16, 32 (segment
+    length m / L); the lazy-F corrective factor C (correction-loop j-steps
+    per main-pass j-step) and GCUPS of lazy-F and scan-F on the same layout."""
+    import numpy as np
+    import torch
+
+    from paper_1909_00899_gb300 import sw, synth
+    torch.cuda.set_device(0)
+    w = synth.workload_protein_scale(n_db=args.n_db, qlens=(256, 512))
+    M = w["M"]
+    db_d = torch.from_numpy(w["db"]).cuda()
+    off_d = torch.from_numpy(w["off"]).cuda()
+    h = sw.Database(db_d, off_d)
+    st = torch.cuda.current_stream()
+    out = torch.empty(h.n, dtype=torch.int32, device="cuda")
+    steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+    total = int(w["off"][-1])
+    rows = []
+    for q, layouts in ((w["queries"][0], ((8, 32), (16, 16), (32, 8))), (w["queries"][1], ((16, 32), (32, 16)))):
+        cells = len(q) * total
+        for L, S in layouts:
+            prof = sw.Profile(q, M, sw.SW_LANE_I32, lanes=L, seg_len=S)
+            scan = lambda: sw.sw_align_db(prof, h, w["o"], w["e"], out, stream=st)
+            lazy = lambda: sw.sw_align_lazyf_db_stats(prof, h, w["o"], w["e"], out, lazy_steps=steps, stream=st)
+            scan()
+            sms = _events_ms(scan, st, 2)
+            lazy()
+            steps.zero_()
+            lazy()
+            torch.cuda.synchronize()
+            c_fac = float(steps.item()) * 32 / cells
+            lms = _events_ms(lazy, st, 2)
+            rows.append({"m": len(q), "lanes": L, "seg_len": S, "lazyf_C": c_fac,
+                         "scan_gcups": cells / (sms * 1e-3) / 1e9, "lazyf_gcups": cells / (lms * 1e-3) / 1e9,
+                         "scan_vs_lazyf": lms / sms})
+            prof.free()
+    line = {"metric": "lazy-F corrective factor and GCUPS vs lanes per alignment (int32)",
+            "value": max(r["scan_vs_lazyf"] for r in rows), "unit": "x (scan-F over lazy-F, best width)",
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "protein queries m=256, 512 vs %d log-normal sequences (%d residues), o=11 e=1"
+                                   % (h.n, total)},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
 
 
 def _pairs_subset(w, ids):

@@ -90,7 +90,7 @@ int sw_profile_build(const uint8_t *query, int32_t qlen,
  * positions per lane (segLen); both 0 selects the built-in table.  Only the
  * shapes the kernels are compiled for are accepted (SW_ERR_INVALID
  * otherwise): int32 {4x8, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16,
- * 16x32, 32x32}, s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
+ * 8x32, 16x32, 32x32}, s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
  * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}, split s16x2 (virtual lanes)
  * {16x8, 32x8, 64x8, 64x16, 64x32}.  Used by the autotuner.
  */

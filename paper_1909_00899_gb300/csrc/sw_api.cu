@@ -100,14 +100,15 @@ const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
 // split-query s16x2: virtual lanes (two per thread)
 const Choice kQ16[] = {{16, 8}, {32, 8}, {64, 8}, {64, 16}, {64, 32}};
 // every (lanes, segment length) the batch kernels are instantiated for
-const Choice kAllI32[] = {{4, 8}, {8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 32}};
+const Choice kAllI32[] = {{4, 8},  {8, 8},   {8, 16},  {16, 8},  {16, 16}, {32, 8},
+                          {32, 12}, {32, 16}, {8, 32},  {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
 
 bool plan_supported(int lane, int L, int S)
 {
     const Choice *t = lane == SW_LANE_I32 ? kAllI32 : (lane == SW_LANE_I16X2 ? kAllI16 : lane == SW_LANE_I8X4 ? kAllI8 : kQ16);
-    const int n = lane == SW_LANE_I32 ? 10 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 5);
+    const int n = lane == SW_LANE_I32 ? 11 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 5);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;

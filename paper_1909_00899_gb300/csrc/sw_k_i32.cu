@@ -17,6 +17,7 @@ int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
     SWG_CASE(32, 8)
     SWG_CASE(32, 12)
     SWG_CASE(32, 16)
+    SWG_CASE(8, 32)
     SWG_CASE(16, 32)
     SWG_CASE(32, 32)
 #undef SWG_CASE
