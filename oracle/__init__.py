@@ -41,6 +41,13 @@ def lib():
         L.oracle_gotoh_batch.restype = None
         L.oracle_gotoh_batch.argtypes = [_u8p, _i32, _u8p, _i64p, _i64, _i8p,
                                          _i32, _i32, _i32, _i32p, _i32]
+        for name in ("oracle_gotoh_end", "oracle_brute_end"):
+            f = getattr(L, name)
+            f.restype = _i32
+            f.argtypes = [_u8p, _i32, _u8p, _i32, _i8p, _i32, _i32, _i32, _i32p, _i32p]
+        L.oracle_gotoh_end_batch.restype = None
+        L.oracle_gotoh_end_batch.argtypes = [_u8p, _i32, _u8p, _i64p, _i64, _i8p, _i32, _i32, _i32,
+                                             _i32p, _i32p, _i32p, _i32]
         L.oracle_gotoh_pairs.restype = None
         L.oracle_gotoh_pairs.argtypes = [_u8p, _i64p, _u8p, _i64p, _i64, _i8p,
                                          _i32, _i32, _i32, _i32p, _i32]
@@ -127,3 +134,44 @@ def gotoh_pairs(q, q_off, r, r_off, M, o, e, nthreads=None):
                              ro.ctypes.data_as(_i64p), n, Mp, A, o, e,
                              out.ctypes.data_as(_i32p), nthreads)
     return out
+
+
+def gotoh_end(q, r, M, o, e):
+    """(score, q_end, r_end): the first cell in column order (1-based) whose
+    H equals the score; (-1, -1) when the score is 0."""
+    q, qp = _u8(q)
+    r, rp = _u8(r)
+    M, Mp, A = _mat(M)
+    qe, re_ = ctypes.c_int32(), ctypes.c_int32()
+    s = lib().oracle_gotoh_end(qp, len(q), rp, len(r), Mp, A, o, e, ctypes.byref(qe), ctypes.byref(re_))
+    return s, qe.value, re_.value
+
+
+def brute_end(q, r, M, o, e):
+    q, qp = _u8(q)
+    r, rp = _u8(r)
+    M, Mp, A = _mat(M)
+    if len(q) > 9 or len(r) > 9:
+        raise ValueError("brute force is limited to lengths <= 9")
+    qe, re_ = ctypes.c_int32(), ctypes.c_int32()
+    s = lib().oracle_brute_end(qp, len(q), rp, len(r), Mp, A, o, e, ctypes.byref(qe), ctypes.byref(re_))
+    return s, qe.value, re_.value
+
+
+def gotoh_end_batch(query, db, db_off, M, o, e, nthreads=None):
+    """Scores, q_end, r_end (int32[n_db] each) of one query against every
+    db sequence."""
+    query, qp = _u8(query)
+    db, dp = _u8(db)
+    off = np.ascontiguousarray(db_off, dtype=np.int64)
+    M, Mp, A = _mat(M)
+    n = len(off) - 1
+    out = np.zeros(n, dtype=np.int32)
+    qe = np.zeros(n, dtype=np.int32)
+    re_ = np.zeros(n, dtype=np.int32)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    lib().oracle_gotoh_end_batch(qp, len(query), dp, off.ctypes.data_as(_i64p), n, Mp, A, o, e,
+                                 out.ctypes.data_as(_i32p), qe.ctypes.data_as(_i32p),
+                                 re_.ctypes.data_as(_i32p), nthreads)
+    return out, qe, re_

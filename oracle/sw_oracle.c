@@ -13,6 +13,8 @@
  *                         by "H - GapOpen" then "- GapExtend" in Alg. 1/6).
  *   oracle_brute          enumeration of every local alignment (tiny inputs);
  *                         pins oracle_gotoh.
+ *   oracle_gotoh_end,     the end cell of the best alignment (first in column
+ *   oracle_brute_end      order) by the recurrence and by enumeration.
  *   oracle_striped_lazyf  Alg. 1 (striped layout, lazy-F correction loop) in
  *                         the paper's step order, with the readings listed
  *                         in its comment.
@@ -86,6 +88,52 @@ int32_t oracle_gotoh(const uint8_t *query, int32_t m, const uint8_t *ref,
 }
 
 /* ------------------------------------------------------------------------ */
+/* End coordinates of the best local alignment: the first cell, in column-  */
+/* major order (smallest reference position r, then smallest query position */
+/* q, both 1-based), whose H equals the score; (-1, -1) when the score is 0. */
+/* Same recurrence as oracle_gotoh.                                          */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_gotoh_end(const uint8_t *query, int32_t m, const uint8_t *ref,
+                         int32_t n, const int8_t *M, int32_t A, int32_t o,
+                         int32_t e, int32_t *q_end, int32_t *r_end)
+{
+    *q_end = -1;
+    *r_end = -1;
+    if (m <= 0 || n <= 0)
+        return 0;
+    int32_t *Hcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t *Ecol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    for (int32_t q = 0; q <= m; ++q) {
+        Hcol[q] = 0;
+        Ecol[q] = NEG_INF;
+    }
+    int32_t best = 0;
+    for (int32_t r = 1; r <= n; ++r) {
+        const int32_t rc = ref[r - 1];
+        int32_t diag = 0, up = 0, F = NEG_INF;
+        for (int32_t q = 1; q <= m; ++q) {
+            const int32_t Eq = imax(Hcol[q] - o, Ecol[q] - e);
+            const int32_t Fq = imax(up - o, F - e);
+            int32_t H = diag + (int32_t)M[query[q - 1] * A + rc];
+            H = imax(imax(imax(H, Eq), Fq), 0);
+            diag = Hcol[q];
+            Hcol[q] = H;
+            Ecol[q] = Eq;
+            F = Fq;
+            up = H;
+            if (H > best) { /* strictly: keeps the first cell in column order */
+                best = H;
+                *q_end = q;
+                *r_end = r;
+            }
+        }
+    }
+    free(Hcol);
+    free(Ecol);
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Brute force: every alignment of every pair of substrings.  An alignment  */
 /* is a path of steps: match (one query and one reference residue, scored   */
 /* M), query-only (I) or reference-only (D).  A maximal run of k steps of   */
@@ -97,14 +145,25 @@ typedef struct {
     int32_t m, n, A, o, e;
     const int8_t *M;
     int32_t best;
+    int32_t best_q, best_r; /* end cell of the best path (1-based), first in column order */
 } brute_ctx;
 
 static void brute_walk(brute_ctx *c, int32_t i, int32_t j, int32_t last,
                        int32_t score)
 {
-    /* last: 0 = match or start, 1 = query-only gap, 2 = reference-only gap */
-    if (score > c->best)
+    /* last: 0 = match or start, 1 = query-only gap, 2 = reference-only gap.
+     * A path that has consumed query residues up to i and reference residues
+     * up to j ends in cell (i, j); only paths whose last step is a match end
+     * a maximal alignment (a trailing gap only lowers the score). */
+    if (score > c->best) {
         c->best = score;
+        c->best_q = i;
+        c->best_r = j;
+    } else if (score == c->best && score > 0 && last == 0 && i > 0 && j > 0 &&
+               (j < c->best_r || (j == c->best_r && i < c->best_q))) {
+        c->best_q = i;
+        c->best_r = j;
+    }
     if (i < c->m && j < c->n)
         brute_walk(c, i + 1, j + 1, 0, score + c->M[c->q[i] * c->A + c->r[j]]);
     if (i < c->m)
@@ -113,17 +172,34 @@ static void brute_walk(brute_ctx *c, int32_t i, int32_t j, int32_t last,
         brute_walk(c, i, j + 1, 2, score - (last == 2 ? c->e : c->o));
 }
 
+static int32_t brute_run(brute_ctx *c)
+{
+    if (c->m > 9 || c->n > 9)
+        return -1; /* refuse: exponential */
+    for (int32_t i0 = 0; i0 < c->m; ++i0)
+        for (int32_t j0 = 0; j0 < c->n; ++j0)
+            brute_walk(c, i0, j0, 0, 0);
+    return c->best;
+}
+
 int32_t oracle_brute(const uint8_t *query, int32_t m, const uint8_t *ref,
                      int32_t n, const int8_t *M, int32_t A, int32_t o,
                      int32_t e)
 {
-    brute_ctx c = {query, ref, m, n, A, o, e, M, 0};
-    if (m > 9 || n > 9)
-        return -1; /* refuse: exponential */
-    for (int32_t i0 = 0; i0 < m; ++i0)
-        for (int32_t j0 = 0; j0 < n; ++j0)
-            brute_walk(&c, i0, j0, 0, 0);
-    return c.best;
+    brute_ctx c = {query, ref, m, n, A, o, e, M, 0, -1, -1};
+    return brute_run(&c);
+}
+
+/* end cell of the best alignment by enumeration (-1, -1 when the score is 0) */
+int32_t oracle_brute_end(const uint8_t *query, int32_t m, const uint8_t *ref,
+                         int32_t n, const int8_t *M, int32_t A, int32_t o,
+                         int32_t e, int32_t *q_end, int32_t *r_end)
+{
+    brute_ctx c = {query, ref, m, n, A, o, e, M, 0, -1, -1};
+    const int32_t s = brute_run(&c);
+    *q_end = s > 0 ? c.best_q : -1;
+    *r_end = s > 0 ? c.best_r : -1;
+    return s;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -394,6 +470,50 @@ static void run_batch(batch_job *b, int32_t nthreads)
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
     for (int32_t t = 0; t < nthreads; ++t)
         pthread_create(&th[t], NULL, batch_worker, b);
+    for (int32_t t = 0; t < nthreads; ++t)
+        pthread_join(th[t], NULL);
+    free(th);
+}
+
+typedef struct {
+    const uint8_t *q;
+    int32_t m;
+    const uint8_t *r;
+    const int64_t *roff;
+    int64_t n;
+    const int8_t *M;
+    int32_t A, o, e;
+    int32_t *out, *qe, *re;
+    int64_t next;
+} ends_job;
+
+static void *ends_worker(void *arg)
+{
+    ends_job *b = (ends_job *)arg;
+    for (;;) {
+        const int64_t start = __atomic_fetch_add(&b->next, 16, __ATOMIC_RELAXED);
+        if (start >= b->n)
+            break;
+        const int64_t stop = start + 16 < b->n ? start + 16 : b->n;
+        for (int64_t k = start; k < stop; ++k)
+            b->out[k] = oracle_gotoh_end(b->q, b->m, b->r + b->roff[k], (int32_t)(b->roff[k + 1] - b->roff[k]),
+                                         b->M, b->A, b->o, b->e, &b->qe[k], &b->re[k]);
+    }
+    return NULL;
+}
+
+/* scores and end cells of one query against n_db sequences */
+void oracle_gotoh_end_batch(const uint8_t *query, int32_t m, const uint8_t *db,
+                            const int64_t *db_off, int64_t n_db, const int8_t *M,
+                            int32_t A, int32_t o, int32_t e, int32_t *out,
+                            int32_t *q_end, int32_t *r_end, int32_t nthreads)
+{
+    ends_job b = {query, m, db, db_off, n_db, M, A, o, e, out, q_end, r_end, 0};
+    if (nthreads < 1)
+        nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int32_t t = 0; t < nthreads; ++t)
+        pthread_create(&th[t], NULL, ends_worker, &b);
     for (int32_t t = 0; t < nthreads; ++t)
         pthread_join(th[t], NULL);
     free(th);

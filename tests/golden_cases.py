@@ -50,5 +50,6 @@ def load():
             q=_expand(s["query"], alpha),
             r=_expand(s["ref"], alpha),
             score=int(s["score"]),
+            end=tuple(int(x) for x in s["end"].split()) if "end" in s else None,
         ))
     return cases

@@ -208,3 +208,47 @@ def test_threaded_batch_and_pairs_equal_single_calls():
     outp = oracle.gotoh_pairs(qs, qoff, db, off, M, 11, 1, nthreads=3)
     for k in range(50):
         assert outp[k] == oracle.gotoh(qs[qoff[k]:qoff[k + 1]], db[off[k]:off[k + 1]], M, 11, 1)
+
+
+@pytest.mark.parametrize("A", [2, 4, 20])
+def test_end_cell_equals_brute_force(A):
+    """The end cell (first in column order among cells whose H is the score)
+    of the recurrence equals the end of the best enumerated alignment."""
+    rng = np.random.default_rng([90, A])
+    for _ in range(2000):
+        M, q, r = _rand_case(rng, A, 6, 6)
+        o = int(rng.integers(1, 13))
+        e = int(rng.integers(0, o + 1))
+        assert oracle.gotoh_end(q, r, M, o, e) == oracle.brute_end(q, r, M, o, e)
+
+
+@pytest.mark.parametrize("case", [c for c in load_golden() if c["end"] is not None], ids=lambda c: c["name"])
+def test_golden_end_cells(case):
+    s, qe, re_ = oracle.gotoh_end(case["q"], case["r"], case["M"], case["o"], case["e"])
+    assert s == case["score"] and (qe, re_) == case["end"], case["cite"]
+
+
+def test_end_cell_of_a_prefix_match():
+    """A query that is a prefix of the reference (identical residues, the
+    seeded protein matrix): the alignment ends at the query's last residue,
+    reference position m."""
+    rng = np.random.default_rng(91)
+    for _ in range(20):
+        M = synth.protein_matrix(rng)
+        q = synth.residues(rng, int(rng.integers(5, 80)), 20)
+        r = np.concatenate([q, synth.residues(rng, int(rng.integers(0, 50)), 20)])
+        s, qe, re_ = oracle.gotoh_end(q, r, M, 11, 1)
+        assert s == int(M[q, q].sum()) and qe == len(q)
+        assert re_ >= len(q)  # an equal score cannot end earlier than the full diagonal
+        assert oracle.gotoh(q, r[:re_], M, 11, 1) == s
+        assert oracle.gotoh(q, r[:re_ - 1], M, 11, 1) < s
+
+
+def test_end_batch_matches_single():
+    rng = np.random.default_rng(92)
+    M = synth.protein_matrix(rng)
+    q = synth.residues(rng, 70, 20)
+    db, off = synth.random_db(rng, 40, 20, "uniform", lo=0, hi=90)
+    s, qe, re_ = oracle.gotoh_end_batch(q, db, off, M, 11, 1, nthreads=3)
+    for k in range(40):
+        assert (s[k], qe[k], re_[k]) == oracle.gotoh_end(q, db[off[k]:off[k + 1]], M, 11, 1)
