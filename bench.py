@@ -56,7 +56,7 @@ def parse():
                     help="comma-separated query lengths (profiling cases)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no oracle check, lazy-F, e2e, probe or CPU baseline")
-    ap.add_argument("--workload", default="scale", choices=["scale", "pairs", "ragged", "serve", "width"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "pairs", "ragged", "serve", "width", "ends"],
                     help="scale: the default line; pairs/ragged/serve: the other workloads")
     ap.add_argument("--n-pairs", type=int, default=1_000_000)
     ap.add_argument("--n-queries", type=int, default=64, help="ragged: queries taken from the 10,000")
@@ -209,7 +209,8 @@ def main():
     if args.workload != "scale":
         from paper_1909_00899_gb300 import build as libbuild
         libbuild.build()
-        {"pairs": run_pairs, "ragged": run_ragged, "serve": run_serve, "width": run_width}[args.workload](args)
+        {"pairs": run_pairs, "ragged": run_ragged, "serve": run_serve, "width": run_width,
+         "ends": run_ends}[args.workload](args)
         return
     import numpy as np
     import torch
@@ -627,6 +628,47 @@ def run_width(args):
             "rows": rows}
     print(json.dumps(line), flush=True)
 
+
+
+def run_ends(args):
+    """Cost of end cells: scores only (automatic layout and int32) against
+    scores with end cells (int32), one query at a time against the scale
+    database."""
+    import numpy as np
+    import torch
+
+    from paper_1909_00899_gb300 import sw, synth
+    torch.cuda.set_device(0)
+    w = synth.workload_protein_scale(n_db=args.n_db, qlens=(512, 2048))
+    M = w["M"]
+    db_d = torch.from_numpy(w["db"]).cuda()
+    off_d = torch.from_numpy(w["off"]).cuda()
+    n = len(w["off"]) - 1
+    total = int(w["off"][-1])
+    st = torch.cuda.current_stream()
+    sc = torch.empty(n, dtype=torch.int32, device="cuda")
+    qe = torch.empty(n, dtype=torch.int32, device="cuda")
+    re_ = torch.empty(n, dtype=torch.int32, device="cuda")
+    rows = []
+    for q in w["queries"]:
+        cells = len(q) * total
+        pa = sw.Profile(q, M)
+        p32 = sw.Profile(q, M, sw.SW_LANE_I32)
+        fa = lambda: sw.sw_align_batch(pa, db_d, off_d, w["o"], w["e"], sc, stream=st)
+        f32 = lambda: sw.sw_align_batch(p32, db_d, off_d, w["o"], w["e"], sc, stream=st)
+        fe = lambda: sw.sw_align_batch_ends(p32, db_d, off_d, w["o"], w["e"], sc, qe, re_, stream=st)
+        row = {"m": len(q)}
+        for name, f in (("auto", fa), ("int32", f32), ("int32_ends", fe)):
+            f()
+            row[name + "_gcups"] = cells / (_events_ms(f, st, 2) * 1e-3) / 1e9
+        rows.append(row)
+        pa.free()
+        p32.free()
+    line = {"metric": "GCUPS with end cells vs scores only", "value": rows[-1]["int32_ends_gcups"],
+            "unit": "GCUPS", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "protein queries m=512, 2048 vs %d log-normal sequences, o=11 e=1" % n},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
 
 
 def _pairs_subset(w, ids):

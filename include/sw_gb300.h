@@ -135,6 +135,21 @@ int sw_align_batch(const sw_profile *prof, const uint8_t *db_residues,
                    int32_t gap_extend, int32_t *scores_out, void *cuda_stream);
 
 /*
+ * sw_align_batch_ends — sw_align_batch plus where each best local alignment
+ * ends (what a mate-rescue caller places reads by; Alg. 1's Max only keeps
+ * the score): q_end_out[k], r_end_out[k] = the 1-based query and reference
+ * positions of the first cell, in column order (smallest reference position,
+ * then smallest query position), whose H equals the score; -1, -1 when the
+ * score is 0.  int32 lanes (the profile's int32 layout); about 1.5x the cost
+ * of the score-only call.  q_end_out, r_end_out: device int32[n_db].
+ */
+int sw_align_batch_ends(const sw_profile *prof, const uint8_t *db_residues,
+                        const int64_t *db_offsets, int64_t n_db,
+                        int32_t gap_open, int32_t gap_extend,
+                        int32_t *scores_out, int32_t *q_end_out,
+                        int32_t *r_end_out, void *cuda_stream);
+
+/*
  * sw_align_lazyf_batch — same inputs, outputs and errors as sw_align_batch,
  * computed with the lazy-F correction loop of Alg. 1 (up to p rounds of
  * shift-and-correct per column, leaving as soon as no lane's carried F can

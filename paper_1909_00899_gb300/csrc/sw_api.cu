@@ -20,6 +20,7 @@ int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
 int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_q16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 }  // namespace swg
 
 using swg::Plan;
@@ -265,18 +266,27 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
 
 // pre_order / pre_total: a database handle's persistent length order and
 // residue count (then no order kernels run and nothing is read back).
+// q_end / r_end: end cells wanted (int32 lanes, ENDS kernels)
 int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o, int32_t e,
                int32_t *scores, void *stream, bool lazy, const int32_t *pre_order = nullptr,
-               int64_t pre_total = -1, unsigned long long *lazy_steps = nullptr)
+               int64_t pre_total = -1, unsigned long long *lazy_steps = nullptr, int32_t *q_end = nullptr,
+               int32_t *r_end = nullptr)
 {
     int rc = check_align_args(prof, db, off, n_db, o, e, scores);
     if (rc)
         return rc;
+    const bool ends = q_end != nullptr;
+    if (ends && (!r_end || lazy))
+        return fail(SW_ERR_INVALID, "end cells need q_end and r_end (scan-F only)");
     if (n_db == 0)
         return SW_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (prof->qlen == 0) {
         cudaError_t err = cudaMemsetAsync(scores, 0, sizeof(int32_t) * (size_t)n_db, st);
+        if (err == cudaSuccess && ends)
+            err = cudaMemsetAsync(q_end, 0xff, sizeof(int32_t) * (size_t)n_db, st);
+        if (err == cudaSuccess && ends)
+            err = cudaMemsetAsync(r_end, 0xff, sizeof(int32_t) * (size_t)n_db, st);
         return err == cudaSuccess ? SW_OK : cuda_fail(err, "cudaMemsetAsync");
     }
     int dev = 0;
@@ -286,7 +296,7 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     keep_pool_warm(dev);
     const int sms = num_sms_of(dev);
 
-    int lane = lazy ? SW_LANE_I32 : prof->lane;
+    int lane = (lazy || ends) ? SW_LANE_I32 : prof->lane;
     if (lane != SW_LANE_I32 && !lane_fits(lane, prof, o, e, prof->plan))
         lane = SW_LANE_I32;  // values do not fit the packed lanes: exact int32 throughout
     const Plan main = lane == SW_LANE_I32 ? prof->plan32 : prof->plan;
@@ -353,13 +363,15 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     a.scores = scores;
     a.one = 1;
     a.lazy_steps = lazy_steps;
+    a.q_end = q_end;
+    a.r_end = r_end;
     a.flag_thresh = flag_threshold(lane, o, prof->maxM);
     a.prof = main_prof;
     a.nchunks = main.C;
     for (int c = 0; c < main.C; ++c) {
         a.chunk = c;
         a.counter = counters + c;
-        kr = launch_plan(main, lazy, a, sms, st);
+        kr = ends ? swg::launch_batch_i32_ends(main, a, sms, st) : launch_plan(main, lazy, a, sms, st);
         if (kr)
             return cuda_fail(kr, "batch kernel launch");
     }
@@ -549,6 +561,16 @@ int sw_align_batch(const sw_profile *prof, const uint8_t *db_residues, const int
                    int32_t gap_open, int32_t gap_extend, int32_t *scores_out, void *cuda_stream)
 {
     return align_impl(prof, db_residues, db_offsets, n_db, gap_open, gap_extend, scores_out, cuda_stream, false);
+}
+
+int sw_align_batch_ends(const sw_profile *prof, const uint8_t *db_residues, const int64_t *db_offsets,
+                        int64_t n_db, int32_t gap_open, int32_t gap_extend, int32_t *scores_out,
+                        int32_t *q_end_out, int32_t *r_end_out, void *cuda_stream)
+{
+    if (n_db > 0 && (!q_end_out || !r_end_out))
+        return fail(SW_ERR_INVALID, "q_end_out / r_end_out is NULL");
+    return align_impl(prof, db_residues, db_offsets, n_db, gap_open, gap_extend, scores_out, cuda_stream, false,
+                      nullptr, -1, nullptr, n_db > 0 ? q_end_out : nullptr, r_end_out);
 }
 
 int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues, const int64_t *db_offsets,

@@ -57,11 +57,17 @@ struct SegPad {
 // pbase[c]: staged profile of cell c; ref + start[c]: the reference residues
 // of cell c, len[c] of them; ncols: warp-uniform number of columns to run
 // (max over the warp).  Returns the group's packed maximum of h (h-space).
-template <class LT, int L, int S, bool LAZY>
+// ENDS (int32 lanes only): also track, per lane, the first cell (column
+// order) where the lane's maximum was reached, and reduce the group's best
+// end cell into end_r / end_q (0-based reference column and position in the
+// chunk, -1 when nothing scored above 0): larger score first, then smaller
+// reference position, then smaller query position.
+template <class LT, int L, int S, bool LAZY, bool ENDS = false>
 __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *const *pbase, const uint8_t *ref,
                                                         const int64_t *start, const int *len, int ncols, int A,
                                                         int o, int e, uint32_t one, bool has_prev, bool has_next,
-                                                        int2 *bnd, int gl, unsigned long long &lazy_steps)
+                                                        int2 *bnd, int gl, unsigned long long &lazy_steps,
+                                                        int *end_r = nullptr, int *end_q = nullptr)
 {
     using T = typename LT::T;
     constexpr int CELLS = LT::CELLS;
@@ -85,6 +91,8 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
     T hlast = k.xinit;    // corrected X of the last position, previous column
     T hb_prev = k.xinit;  // previous chunk's last X at the previous column
     T mx = k.hzero;
+    static_assert(!ENDS || (LT::CELLS == 1 && !LAZY), "end cells: int32 scan-F only");
+    int best_r = -1, best_j = 0;  // first cell of this lane's maximum (ENDS)
 
     for (int r0 = 0; r0 < ncols; r0 += L) {
         int myres[CELLS];
@@ -146,12 +154,19 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                         X[j] = LT::addmax(F, k.negO, ho);
                         E[j] = LT::e_next(Ej, X[j], k);
                         F = LT::addmax(F, k.negE, ho);
-                        if (j & 1)
+                        if constexpr (ENDS) {
+                            if (h > mx) {
+                                mx = h;
+                                best_r = r;
+                                best_j = j;
+                            }
+                        } else if (j & 1) {
                             mx = LT::max3(mx, hpair, h);
-                        else if (j == S - 1)
+                        } else if (j == S - 1) {
                             mx = LT::max2(mx, h);
-                        else
+                        } else {
                             hpair = h;
+                        }
                     }
                 } else {
 #pragma unroll
@@ -164,12 +179,19 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                         X[j] = LT::addmax(F, k.negO, ho);
                         E[j] = LT::e_next(E[j], X[j], k);
                         F = LT::addmax(F, k.negE, ho);
-                        if (j & 1)
+                        if constexpr (ENDS) {
+                            if (h > mx) {
+                                mx = h;
+                                best_r = r;
+                                best_j = j;
+                            }
+                        } else if (j & 1) {
                             mx = LT::max3(mx, hpair, h);
-                        else if (j == S - 1)
+                        } else if (j == S - 1) {
                             mx = LT::max2(mx, h);
-                        else
+                        } else {
                             hpair = h;
+                        }
                     }
                 }
                 // max-plus prefix scan of the F leaving each lane (log2 L steps)
@@ -242,6 +264,23 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
             }
         }
     }
+    if constexpr (ENDS) {
+        int bq = gl * S + best_j;
+#pragma unroll
+        for (int dd = L / 2; dd >= 1; dd >>= 1) {
+            const T om = __shfl_xor_sync(FULL, mx, dd, L);
+            const int orr = __shfl_xor_sync(FULL, best_r, dd, L);
+            const int oq = __shfl_xor_sync(FULL, bq, dd, L);
+            if (om > mx || (om == mx && (orr < best_r || (orr == best_r && oq < bq)))) {
+                mx = om;
+                best_r = orr;
+                bq = oq;
+            }
+        }
+        *end_r = mx > 0 ? best_r : -1;
+        *end_q = mx > 0 ? bq : -1;
+        return mx;
+    }
 #pragma unroll
     for (int dd = L / 2; dd >= 1; dd >>= 1)
         mx = LT::max2(mx, __shfl_xor_sync(FULL, mx, dd, L));
@@ -305,7 +344,7 @@ __device__ __forceinline__ void stage_profile(typename LT::Elem *dst, int A, int
     }
 }
 
-template <class LT, int L, int S, bool LAZY>
+template <class LT, int L, int S, bool LAZY, bool ENDS = false>
 __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs p)
 {
     using T = typename LT::T;
@@ -363,10 +402,31 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
             my_n = max(my_n, len[c]);
         }
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
-        const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
-                                                  has_prev, has_next, p.bnd, gl, lazy_steps);
-        if (gl == 0)
-            write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), seq, has_prev, p.flag_thresh, p.scores);
+        if constexpr (ENDS) {
+            int er = -1, eq = -1;
+            const T mx = striped_unit<LT, L, S, false, true>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
+                                                             has_prev, has_next, p.bnd, gl, lazy_steps, &er, &eq);
+            if (gl == 0 && seq[0] >= 0) {
+                // combine with the earlier chunks (smaller query positions)
+                int s = (int)mx, qe = eq >= 0 ? qbase + eq + 1 : -1, re = er >= 0 ? er + 1 : -1;
+                if (has_prev) {
+                    const int ps = p.scores[seq[0]], pq = p.q_end[seq[0]], pr = p.r_end[seq[0]];
+                    if (!(s > ps || (s == ps && s > 0 && (re < pr || (re == pr && qe < pq))))) {
+                        s = ps;
+                        qe = pq;
+                        re = pr;
+                    }
+                }
+                p.scores[seq[0]] = s;
+                p.q_end[seq[0]] = s > 0 ? qe : -1;
+                p.r_end[seq[0]] = s > 0 ? re : -1;
+            }
+        } else {
+            const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
+                                                      has_prev, has_next, p.bnd, gl, lazy_steps);
+            if (gl == 0)
+                write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), seq, has_prev, p.flag_thresh, p.scores);
+        }
     }
     // j-steps of the correction loop, counted once per warp
     if (LAZY && p.lazy_steps && lane == 0 && lazy_steps)

@@ -32,6 +32,8 @@ struct BatchArgs {
     unsigned long long *lazy_steps;  // optional statistics of the lazy-F loop
     uint32_t one;             // 1 (a run-time multiplier for FMA-pipe additions)
     int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
+    int32_t *q_end;           // end cells (1-based query / reference position), ENDS kernels
+    int32_t *r_end;
 };
 
 // Parameters of the pair kernel (each pair has its own query).

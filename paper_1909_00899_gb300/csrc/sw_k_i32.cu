@@ -24,4 +24,24 @@ int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
     return (int)cudaErrorInvalidValue;
 }
 
+int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
+{
+#define SWG_CASE(LL, SS)              \
+    if (pl.L == LL && pl.S == SS)     \
+        return launch_batch_inst<LaneI32, LL, SS, false, true>(a, num_sms, st);
+    SWG_CASE(4, 8)
+    SWG_CASE(8, 8)
+    SWG_CASE(8, 16)
+    SWG_CASE(16, 8)
+    SWG_CASE(16, 16)
+    SWG_CASE(32, 8)
+    SWG_CASE(32, 12)
+    SWG_CASE(32, 16)
+    SWG_CASE(8, 32)
+    SWG_CASE(16, 32)
+    SWG_CASE(32, 32)
+#undef SWG_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
 }  // namespace swg

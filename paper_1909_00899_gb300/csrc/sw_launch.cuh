@@ -6,10 +6,10 @@
 
 namespace swg {
 
-template <class LT, int L, int S, bool LAZY>
+template <class LT, int L, int S, bool LAZY, bool ENDS = false>
 int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-    auto kern = sw_batch_kernel<LT, L, S, LAZY>;
+    auto kern = sw_batch_kernel<LT, L, S, LAZY, ENDS>;
     constexpr size_t kMaxSmem = (size_t)33 * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;

@@ -33,6 +33,7 @@ EXPORTS = (
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
+    "sw_align_batch_ends",
 )
 
 
@@ -70,6 +71,8 @@ def lib():
             f = getattr(L, name)
             f.restype = ctypes.c_int
             f.argtypes = [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp]
+        L.sw_align_batch_ends.restype = ctypes.c_int
+        L.sw_align_batch_ends.argtypes = [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
         L.sw_align_pairs.restype = ctypes.c_int
         L.sw_align_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
         L.sw_db_create.restype = ctypes.c_int
@@ -199,6 +202,21 @@ def sw_align_batch(profile, db_residues, db_offsets, gap_open, gap_extend, score
     """Scan-F (Alg. 6) scores of profile's query against every db sequence."""
     return _align(lib().sw_align_batch, profile, db_residues, db_offsets, gap_open, gap_extend,
                   scores_out, stream)
+
+
+def sw_align_batch_ends(profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, q_end_out,
+                        r_end_out, stream=None):
+    """Scores and end cells (1-based query / reference position of the first
+    cell in column order reaching the score; -1 when the score is 0)."""
+    n_db = int(db_offsets.numel()) - 1
+    for t in (scores_out, q_end_out, r_end_out):
+        if t.numel() < n_db:
+            raise ValueError("output too small")
+    _check(lib().sw_align_batch_ends(profile.handle, _dev_ptr(db_residues, "uint8"),
+                                     _dev_ptr(db_offsets, "int64"), n_db, int(gap_open), int(gap_extend),
+                                     _dev_ptr(scores_out, "int32"), _dev_ptr(q_end_out, "int32"),
+                                     _dev_ptr(r_end_out, "int32"), _stream(stream)))
+    return scores_out, q_end_out, r_end_out
 
 
 def sw_align_lazyf_batch(profile, db_residues, db_offsets, gap_open, gap_extend, scores_out, stream=None):

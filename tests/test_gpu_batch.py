@@ -273,3 +273,53 @@ def test_lazyf_pairs_exact_and_counts_steps(sw):
     torch.cuda.synchronize()
     unrelated = int(steps.item())
     assert related > 3 * unrelated
+
+
+@pytest.mark.parametrize("lane", ["auto", "i32"])
+def test_end_cells_match_oracle(sw, lane):
+    """Scores and end cells of every alignment equal the oracle's (first
+    cell in column order), across single- and multi-chunk queries."""
+    rng = np.random.default_rng(1201)
+    M = synth.protein_matrix(rng)
+    lens = np.concatenate([[0, 1, 3], rng.integers(1, 600, 150)])
+    db, off = synth.pack(lens.astype(np.int64), rng, 20)
+    db_d, off_d = db_to_dev(db, off)
+    n = len(off) - 1
+    kind = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32}[lane]
+    for qlen in (1, 40, 300, 700, 1500):
+        q = synth.residues(rng, qlen, 20)
+        ws, wq, wr = oracle.gotoh_end_batch(q, db, off, M, 11, 1)
+        prof = sw.Profile(q, M, kind)
+        sc = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        qe = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        re_ = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        sw.sw_align_batch_ends(prof, db_d, off_d, 11, 1, sc, qe, re_)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(sc.cpu().numpy(), ws, err_msg="qlen=%d" % qlen)
+        np.testing.assert_array_equal(re_.cpu().numpy(), wr, err_msg="qlen=%d" % qlen)
+        np.testing.assert_array_equal(qe.cpu().numpy(), wq, err_msg="qlen=%d" % qlen)
+        prof.free()
+
+
+def test_end_cells_of_planted_local_matches(sw):
+    """Reads planted inside random references: the end cell is where the
+    planted copy ends (DNA scoring, high identity)."""
+    rng = np.random.default_rng(1202)
+    M = synth.dna_matrix()
+    q = synth.residues(rng, 120, 4)
+    refs, ends = [], []
+    for k in range(50):
+        pre = int(rng.integers(0, 300))
+        refs.append(np.concatenate([synth.residues(rng, pre, 4), q, synth.residues(rng, 200, 4)]))
+        ends.append(pre + 120)
+    db, off = pack_list(refs)
+    db_d, off_d = db_to_dev(db, off)
+    prof = sw.Profile(q, M)
+    sc = torch.empty(50, dtype=torch.int32, device="cuda")
+    qe = torch.empty(50, dtype=torch.int32, device="cuda")
+    re_ = torch.empty(50, dtype=torch.int32, device="cuda")
+    sw.sw_align_batch_ends(prof, db_d, off_d, 6, 1, sc, qe, re_)
+    torch.cuda.synchronize()
+    assert (sc.cpu().numpy() == 120).all()
+    assert (qe.cpu().numpy() == 120).all()
+    np.testing.assert_array_equal(re_.cpu().numpy(), np.array(ends))
