@@ -29,8 +29,10 @@
  *    then returns a message (thread-local, valid until the next call on the
  *    same thread).  Invalid arguments are rejected before any CUDA call.
  *  - Library scratch (length-sorted work order, boundary rows of long
- *    queries, overflow lists) comes from a library-owned stream-ordered
- *    memory pool and is released on the call's stream.
+ *    queries, overflow lists) is allocated with cudaMallocAsync on the call's
+ *    stream from the device's default memory pool and released on that
+ *    stream; the library raises that pool's release threshold once per
+ *    device so freed scratch stays cached between calls.
  */
 #ifndef SW_GB300_H
 #define SW_GB300_H
@@ -153,7 +155,9 @@ int sw_align_batch_ends(const sw_profile *prof, const uint8_t *db_residues,
  * sw_align_lazyf_batch — same inputs, outputs and errors as sw_align_batch,
  * computed with the lazy-F correction loop of Alg. 1 (up to p rounds of
  * shift-and-correct per column, leaving as soon as no lane's carried F can
- * raise anything).  Always int32 lanes.  The comparison kernel.
+ * raise anything).  Runs on the profile's layout when it is int32 or
+ * two-alignment s16x2 (flagged s16x2 alignments are rescored with the
+ * scan-F int32 kernel), on the int32 layout otherwise.  The comparison.
  */
 int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues,
                          const int64_t *db_offsets, int64_t n_db,

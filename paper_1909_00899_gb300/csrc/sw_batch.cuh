@@ -231,8 +231,7 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                         hpair = h;
                 }
                 // lazy-F (Alg. 1): shift the carry into the next lane and
-                // correct, for at most L rounds (int32 lanes: X-space and
-                // h-space coincide)
+                // correct, for at most L rounds
                 T fb = F;  // F leaving this lane, corrected as rounds pass
                 T Fc = __shfl_up_sync(FULL, F, 1, L);
                 if (gl == 0)
@@ -243,10 +242,10 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                     for (int j = 0; j < S; ++j) {
                         const T hold = X[j];
                         X[j] = LT::addmax(Fc, k.negO, hold);
-                        E[j] = LT::max2(E[j], X[j]);
-                        Fc = Fc + k.negE;  // plain add: this loop is latency-bound
+                        E[j] = LT::e_raise(E[j], X[j], k);
+                        Fc = LT::lazy_step(Fc, k);  // plain add: this loop is latency-bound
                         ++lazy_steps;
-                        if (__all_sync(FULL, Fc <= max(hold, 0))) {
+                        if (__all_sync(FULL, LT::lazy_dominated(Fc, hold, k))) {
                             done = true;
                             break;
                         }
@@ -259,8 +258,12 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                     }
                 }
                 hlast = X[S - 1];
-                if (has_next && gl == L - 1 && r < len[0])
-                    bnd[start[0] + r] = make_int2(LT::x_true(hlast, 0), LT::x_true(fb, 0));
+                if (has_next && gl == L - 1) {
+#pragma unroll
+                    for (int c = 0; c < CELLS; ++c)
+                        if (r < len[c])
+                            bnd[start[c] + r] = make_int2(LT::x_true(hlast, c), LT::x_true(fb, c));
+                }
             }
         }
     }
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
     constexpr int QC = L * S;
     constexpr unsigned FULL = 0xffffffffu;
     static_assert(L >= 2 && L <= 32 && (L & (L - 1)) == 0, "lanes per alignment: power of two");
-    static_assert(!LAZY || CELLS == 1, "lazy-F kernel uses int32 lanes");
+    static_assert(!LAZY || LT::VEC != 16, "lazy-F kernel: int32 or s16x2 lanes");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Elem *sprof = reinterpret_cast<Elem *>(smem_raw);

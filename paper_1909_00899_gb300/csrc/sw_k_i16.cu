@@ -3,11 +3,12 @@
 
 namespace swg {
 
-int launch_batch_i16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
+int launch_batch_i16(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-#define SWG_CASE(LL, SS)                          \
-    if (pl.L == LL && pl.S == SS)                 \
-        return launch_batch_inst<LaneI16x2, LL, SS, false>(a, num_sms, st);
+#define SWG_CASE(LL, SS)                                                          \
+    if (pl.L == LL && pl.S == SS)                                                 \
+        return lazy ? launch_batch_inst<LaneI16x2, LL, SS, true>(a, num_sms, st)  \
+                    : launch_batch_inst<LaneI16x2, LL, SS, false>(a, num_sms, st);
     SWG_CASE(8, 8)
     SWG_CASE(8, 16)
     SWG_CASE(16, 8)

@@ -91,6 +91,12 @@ struct LaneI32 {
     __device__ __forceinline__ static int x_true(T v, int) { return v; }
     __device__ __forceinline__ static T x_pack(const int *v) { return v[0]; }
 
+    // lazy-F loop (Alg. 1): E raised from a corrected X; the carry Fc (after
+    // the extend step) is dominated when Fc <= max(X before the raise, 0)
+    __device__ __forceinline__ static T e_raise(T E, T X, const K &) { return max(E, X); }
+    __device__ __forceinline__ static T lazy_step(T Fc, const K &k) { return Fc + k.negE; }
+    __device__ __forceinline__ static bool lazy_dominated(T Fc, T hold, const K &) { return Fc <= max(hold, 0); }
+
     // Profile rows of residues res[c] for segment positions 0..S-1; base[c]
     // is cell c's staged profile, layout [residue][SP/VEC][lane][VEC].
     // profile vector k (positions VEC*k .. VEC*k+VEC-1) of the residues res[c]
@@ -200,6 +206,15 @@ struct LaneI16x2 {
     __device__ __forceinline__ static T x_pack(const int *v)
     {
         return (uint32_t)((v[0] + BX) & 0xffff) | ((uint32_t)((v[1] + BX) & 0xffff) << 16);
+    }
+
+    // lazy-F loop: E (h-space) raised from X (X-space); both halves dominated
+    __device__ __forceinline__ static T e_raise(T E, T X, const K &k) { return __viaddmax_s16x2(X, k.delta, E); }
+    __device__ __forceinline__ static T lazy_step(T Fc, const K &k) { return Fc + k.negE32; }
+    __device__ __forceinline__ static bool lazy_dominated(T Fc, T hold, const K &k)
+    {
+        const T t = __vmaxs2(hold, k.xzero);
+        return __vmaxs2(Fc, t) == t;
     }
 
     template <int L, int SP>

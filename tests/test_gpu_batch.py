@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-LANES = ["i32", "i16x2", "i16x2q", "i8x4", "auto", "lazyf"]
+LANES = ["i32", "i16x2", "i16x2q", "i8x4", "auto", "lazyf", "lazyf16"]
 
 
 @pytest.fixture(scope="module")
@@ -26,11 +26,12 @@ def sw():
 
 def run(sw, kind, query, M, db_d, off_d, o, e):
     lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i16x2q": sw.SW_LANE_I16X2Q,
-            "i8x4": sw.SW_LANE_I8X4, "auto": sw.SW_LANE_AUTO, "lazyf": sw.SW_LANE_I32}[kind]
+            "i8x4": sw.SW_LANE_I8X4, "auto": sw.SW_LANE_AUTO, "lazyf": sw.SW_LANE_I32,
+            "lazyf16": sw.SW_LANE_I16X2}[kind]
     prof = sw.Profile(query, M, lane)
     n = off_d.numel() - 1
     out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
-    if kind == "lazyf":
+    if kind.startswith("lazyf"):
         sw.sw_align_lazyf_batch(prof, db_d, off_d, o, e, out)
     else:
         sw.sw_align_batch(prof, db_d, off_d, o, e, out)
