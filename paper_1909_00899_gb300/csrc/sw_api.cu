@@ -369,6 +369,7 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     a.q_end = q_end;
     a.r_end = r_end;
     a.flag_thresh = flag_threshold(lane, o, prof->maxM);
+    a.min_m = prof->minM;
     a.prof = main_prof;
     a.nchunks = main.C;
     for (int c = 0; c < main.C; ++c) {
@@ -696,11 +697,13 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
 
     swg::PairArgs a;
     memset(&a, 0, sizeof(a));
-    int32_t maxM = -128;
+    int32_t maxM = -128, minM = 127;
     for (int i = 0; i < alphabet * alphabet; ++i) {
         a.M[i] = subst_matrix[i];
         maxM = std::max<int32_t>(maxM, subst_matrix[i]);
+        minM = std::min<int32_t>(minM, subst_matrix[i]);
     }
+    a.min_m = minM;
     sw_profile shape;  // only the matrix range is read by lane_fits
     shape.maxM = maxM;
     int lane = lazy ? SW_LANE_I32 : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type);

@@ -146,14 +146,26 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                     for (int j = 0; j < S; ++j) {
                         if (j % V == 0)
                             LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
-                        const T Ej = LT::max2(E[j], d);
-                        const T h = LT::h_of(hd, Pv[j % V], Ej, k);
-                        hd = LT::xd_corr(X[j], d, k);
-                        d = LT::dstep(d, k);
-                        const T ho = LT::ho_of(h, k);
-                        X[j] = LT::addmax(F, k.negO, ho);
-                        E[j] = LT::e_next(Ej, X[j], k);
-                        F = LT::addmax(F, k.negE, ho);
+                        T h;
+                        if constexpr (LT::D0) {
+                            // d_j is dominated in h by the raised diagonal
+                            h = LT::h_of(hd, Pv[j % V], E[j], k);
+                            hd = LT::xd_corr(X[j], d, k);
+                            d = LT::dstep(d, k);
+                            const T ho = LT::ho_of(h, k);
+                            X[j] = LT::addmax(F, k.negO, ho);
+                            E[j] = LT::e_next_corr(E[j], d, X[j], k);
+                            F = LT::addmax(F, k.negE, ho);
+                        } else {
+                            const T Ej = LT::max2(E[j], d);
+                            h = LT::h_of(hd, Pv[j % V], Ej, k);
+                            hd = LT::xd_corr(X[j], d, k);
+                            d = LT::dstep(d, k);
+                            const T ho = LT::ho_of(h, k);
+                            X[j] = LT::addmax(F, k.negO, ho);
+                            E[j] = LT::e_next(Ej, X[j], k);
+                            F = LT::addmax(F, k.negE, ho);
+                        }
                         if constexpr (ENDS) {
                             if (h > mx) {
                                 mx = h;

@@ -34,6 +34,8 @@ struct BatchArgs {
     int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
     int32_t *q_end;           // end cells (1-based query / reference position), ENDS kernels
     int32_t *r_end;
+    int32_t min_m;            // smallest substitution score of the profile (the split
+                              // kernels' shorter corrected pass needs min_m >= -o)
 };
 
 // Parameters of the pair kernel (each pair has its own query).
@@ -52,6 +54,7 @@ struct PairArgs {
     uint32_t one;             // 1 (a run-time multiplier for FMA-pipe additions)
     int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
     unsigned long long *lazy_steps;  // optional statistics of the lazy-F loop
+    int32_t min_m;            // smallest substitution score (shorter corrected pass: see sw_lanes.cuh)
 };
 
 // batch launchers (sw_k_i32.cu, sw_k_i16.cu, sw_k_i8.cu), declared in

@@ -1,13 +1,17 @@
-// int32-lane instantiations: scan-F (Alg. 6) and lazy-F (Alg. 1).
+// int32-lane instantiations: scan-F (Alg. 6; the shorter corrected pass of
+// LaneI32D when the matrix allows it) and lazy-F (Alg. 1).
 #include "sw_launch.cuh"
 
 namespace swg {
 
 int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st)
 {
+    // the shorter corrected pass needs every substitution score >= -(o+e)
+    const bool d0 = (int64_t)a.min_m >= -(int64_t)a.o - a.e;
 #define SWG_CASE(LL, SS)                                                              \
     if (pl.L == LL && pl.S == SS)                                                     \
         return lazy ? launch_batch_inst<LaneI32, LL, SS, true>(a, num_sms, st)        \
+               : d0 ? launch_batch_inst<LaneI32D, LL, SS, false>(a, num_sms, st)      \
                     : launch_batch_inst<LaneI32, LL, SS, false>(a, num_sms, st);
     SWG_CASE(4, 8)
     SWG_CASE(8, 8)

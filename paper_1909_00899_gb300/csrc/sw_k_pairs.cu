@@ -8,13 +8,22 @@ namespace swg {
 int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
                  int64_t n_hint, int num_sms, cudaStream_t st)
 {
+    // shorter corrected pass (sw_lanes.cuh): int32 when min(M) >= -(o+e),
+    // s16x2 when min(M) >= -o
+    const bool d0_32 = (int64_t)a.min_m >= -(int64_t)a.o - a.e;
+    const bool d0_16 = a.min_m >= -a.o;
 #define SWG_CASE(LT, LL, SS)                                                        \
     if (L == LL && S == SS)                                                         \
         return launch_pairs_inst<LT, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st);
+#define SWG_CASE16(LL, SS)                                                          \
+    if (L == LL && S == SS)                                                         \
+        return d0_16 ? launch_pairs_inst<LaneI16x2D, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st) \
+                     : launch_pairs_inst<LaneI16x2, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st);
 #define SWG_CASE_LAZY(LL, SS)                                                       \
     if (L == LL && S == SS)                                                         \
-        return lazy ? launch_pairs_inst<LaneI32, LL, SS, true>(a, list, count_dev, n_hint, num_sms, st) \
-                    : launch_pairs_inst<LaneI32, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st);
+        return lazy    ? launch_pairs_inst<LaneI32, LL, SS, true>(a, list, count_dev, n_hint, num_sms, st)  \
+               : d0_32 ? launch_pairs_inst<LaneI32D, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st) \
+                       : launch_pairs_inst<LaneI32, LL, SS, false>(a, list, count_dev, n_hint, num_sms, st);
     if (lane == LK_I32) {
         SWG_CASE_LAZY(4, 8)
         SWG_CASE_LAZY(8, 8)
@@ -23,11 +32,11 @@ int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int
         SWG_CASE_LAZY(32, 8)
         SWG_CASE_LAZY(32, 16)
     } else if (lane == LK_I16X2) {
-        SWG_CASE(LaneI16x2, 8, 8)
-        SWG_CASE(LaneI16x2, 16, 8)
-        SWG_CASE(LaneI16x2, 16, 10)
-        SWG_CASE(LaneI16x2, 32, 8)
-        SWG_CASE(LaneI16x2, 32, 16)
+        SWG_CASE16(8, 8)
+        SWG_CASE16(16, 8)
+        SWG_CASE16(16, 10)
+        SWG_CASE16(32, 8)
+        SWG_CASE16(32, 16)
     } else if (lane == LK_I8X4) {
         SWG_CASE(LaneI8x4, 8, 16)
         SWG_CASE(LaneI8x4, 16, 10)
@@ -35,6 +44,7 @@ int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int
         SWG_CASE(LaneI8x4, 32, 16)
     }
 #undef SWG_CASE
+#undef SWG_CASE16
 #undef SWG_CASE_LAZY
     return (int)cudaErrorInvalidValue;
 }

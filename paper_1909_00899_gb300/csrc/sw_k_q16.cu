@@ -1,15 +1,17 @@
 // Split-query s16x2 instantiations (two query halves of one alignment per
 // register).  Plans count virtual lanes: a plan of 2L lanes runs on L threads.
+// Each layout has the D0 pass (every substitution score >= -o, the usual
+// case) and the general one.
 #include <mutex>
 
 #include "sw_split.cuh"
 
 namespace swg {
 
-template <int L, int S>
+template <int L, int S, bool D0>
 static int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-    auto kern = sw_split_kernel<L, S>;
+    auto kern = sw_split_kernel<L, S, D0>;
     constexpr size_t kMaxSmem = (size_t)33 * L * SegPad<S, 4>::value * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -40,9 +42,11 @@ static int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 
 int launch_batch_q16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-#define SWG_CASE(VL, SS)              \
-    if (pl.L == VL && pl.S == SS)     \
-        return launch_split_inst<VL / 2, SS>(a, num_sms, st);
+    const bool d0 = a.min_m >= -a.o;
+#define SWG_CASE(VL, SS)                                                                     \
+    if (pl.L == VL && pl.S == SS)                                                            \
+        return d0 ? launch_split_inst<VL / 2, SS, true>(a, num_sms, st)                      \
+                  : launch_split_inst<VL / 2, SS, false>(a, num_sms, st);
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
     SWG_CASE(64, 8)

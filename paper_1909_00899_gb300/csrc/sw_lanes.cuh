@@ -17,7 +17,8 @@
 // time, i.e. on the FMA pipe, which leaves the half-rate integer ALU pipe to
 // the max-plus DPX steps.  ALU instructions per register-cell of the plain
 // pass: h (1), X (1), E (1), F (1) and the running max (1/2, vimax3 over two
-// positions); the deferred correction adds 2 (raise E, raise the diagonal).
+// positions); the deferred correction adds 2 (raise E, raise the diagonal),
+// or 1 with the D0 lane types at the end of this file.
 //
 // Packed lanes are exact until H + M leaves the lane range.  The H of the
 // first such addition was exact and already folded into the alignment's
@@ -45,6 +46,7 @@ struct LaneI32 {
     static constexpr int VEC = 4;       // profile elements per 16 bytes
     static constexpr int PAD = -(1 << 24);  // inert staged profile value
     static constexpr bool CROSS = false;    // cells never leak into each other
+    static constexpr bool D0 = false;       // see LaneI32D
     __host__ __device__ static constexpr int prof_bias(int o) { return o; }
 
     struct K {
@@ -83,6 +85,12 @@ struct LaneI32 {
     __device__ __forceinline__ static T dstep(T d, const K &k) { return fadd(d, k.negE, k); }
     // corrected diagonal (X-space) from the stored X and d (h-space)
     __device__ __forceinline__ static T xd_corr(T X, T d, const K &) { return max(X, d); }
+    // next E with the correction of the previous column: max(E - e, d_{j+1}, X)
+    // (dn = d_j - e; h-space = X-space)
+    __device__ __forceinline__ static T e_next_corr(T E, T dn, T X, const K &k)
+    {
+        return __vimax3_s32(fadd(E, k.negE, k), dn, X);
+    }
     __device__ __forceinline__ static bool carry_pos(T c, const K &) { return c > 0; }
     // last position raised by the carry: max(X, c - o - (S-1)e)
     __device__ __forceinline__ static T last_corr(T X, T c, const K &k) { return max(X, fadd(c, k.negOS1, k)); }
@@ -138,6 +146,7 @@ struct LaneI16x2 {
     // once one cell has overflowed the other may be corrupted, so both cells
     // of a register are rescored together
     static constexpr bool CROSS = true;
+    static constexpr bool D0 = false;  // see LaneI16x2D
     __host__ __device__ static constexpr int prof_bias(int) { return PB; }
 
     struct K {
@@ -154,11 +163,14 @@ struct LaneI16x2 {
     }
     // constant whose 32-bit add adds v to both halves
     __device__ __forceinline__ static T splat32(int v) { return (uint32_t)v * 65537u; }
-    __device__ __forceinline__ static K consts(int o, int e, int S, uint32_t one)
+    __device__ __forceinline__ static K consts(int o, int e, int S, uint32_t one) { return consts_pb(o, e, S, one, PB); }
+    // pb: the profile bias actually staged (PB, or o for the split kernel's
+    // pass in which h-space and X-space coincide)
+    __device__ __forceinline__ static K consts_pb(int o, int e, int S, uint32_t one, int pb)
     {
         K k;
         k.one = one;
-        k.bh = BX + PB - o;
+        k.bh = BX + pb - o;
         k.negO = splat(-o);
         k.negE = splat(-e);
         k.delta = splat(k.bh - BX);
@@ -166,7 +178,7 @@ struct LaneI16x2 {
         k.xzero = splat(BX);
         k.hzero = splat(k.bh);
         k.xinit = splat(BX - o);
-        k.hshift32 = splat32(-PB);              // h -> H' - o in X-space
+        k.hshift32 = splat32(-pb);              // h -> H' - o in X-space
         k.negE32 = splat32(-e);
         k.d0c32 = splat32(k.bh - BX - o);       // carry (X) -> d (h): c - o
         k.negOS1_32 = splat32(-o - (S - 1) * e);
@@ -260,6 +272,7 @@ struct LaneI8x4 {
     static constexpr int VEC = 16;
     static constexpr int PAD = -128;
     static constexpr bool CROSS = false;  // saturating bytes never leak
+    static constexpr bool D0 = false;
     __host__ __device__ static constexpr int prof_bias(int o) { return o; }
 
     struct K {
@@ -361,6 +374,41 @@ struct LaneI8x4 {
             for (int t = 0; t < 16; ++t)
                 if (16 * k + t < S) P[16 * k + t] = Q[t];
         }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Shorter corrected pass.  The deferred correction d_j = carry - o - j*e
+// (the carry's F at position j, less o) raises both E[j] and the diagonal
+// of position j+1.  In h it is never needed once every substitution score
+// is >= -(o+e): the corrected H of position j-1 is >= carry - (j-1)*e, so
+// the raised diagonal already gives h >= carry - (j-1)*e + M >= d_j (for
+// j = 0 the diagonal is the previous lane's last position, whose corrected H
+// is >= carry + e because e <= o).  d_j then enters only the next E,
+// max(E - e, d_j - e, X), which needs h-space = X-space.  Per register-cell
+// the corrected pass loses one ALU max.  h itself is unchanged, so scores
+// and end cells are the same as with the general pass.
+//
+// int32: h-space is X-space already; usable when min(M) >= -(o+e).
+struct LaneI32D : LaneI32 {
+    static constexpr bool D0 = true;
+};
+
+// s16x2 with the profile biased by o instead of 128 (h-space = X-space,
+// BH = BX): every staged value M + o must stay >= 0 for the packed adds, so
+// usable when min(M) >= -o.  The inert value 0 reads as M = -o.
+struct LaneI16x2D : LaneI16x2 {
+    static constexpr bool D0 = true;
+    __host__ __device__ static constexpr int prof_bias(int o) { return o; }
+    __device__ __forceinline__ static K consts(int o, int e, int S, uint32_t one)
+    {
+        return consts_pb(o, e, S, one, o);
+    }
+    __device__ __forceinline__ static T e_next(T E, T X, const K &k) { return __viaddmax_s16x2(E, k.negE, X); }
+    __device__ __forceinline__ static T xd_corr(T X, T d, const K &) { return __vmaxs2(X, d); }
+    __device__ __forceinline__ static T e_next_corr(T E, T dn, T X, const K &k)
+    {
+        return __vimax3_s16x2(fadd(E, k.negE32, k), dn, X);
     }
 };
 

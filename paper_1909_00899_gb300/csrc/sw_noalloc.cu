@@ -140,6 +140,7 @@ extern "C" int sw_align_batch_noalloc(const sw_profile *prof, const uint8_t *db,
     a.scores = scores;
     a.one = 1;
     a.flag_thresh = swg::api_flag_threshold(lane, o, prof->maxM);
+    a.min_m = prof->minM;
     a.prof = main_prof;
     a.nchunks = main.C;
     for (int c = 0; c < main.C; ++c) {

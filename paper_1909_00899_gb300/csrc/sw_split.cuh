@@ -14,6 +14,16 @@
 //    half (the low half of lane L-1) is folded into the high halves with
 //    weight (l+1)*S*e, and it is the carry into the high half of lane 0.
 // Values use the biased X-space / h-space of LaneI16x2 (sw_lanes.cuh).
+//
+// D0 (shorter corrected pass): when every substitution score is >= -o the
+// profile is biased by o instead of 128, so h-space and X-space coincide
+// (delta = 0), and the deferred correction d_j no longer has to raise E before
+// h.  The carry reaches cell j through the raised diagonal at least as high:
+// the corrected H of cell j-1 is >= carry - (j-1)e, so the diagonal gives
+// >= carry - (j-1)e + M >= carry - o - je = d_j whenever M >= -(o+e) (for
+// j = 0 the same holds with lane l-1's last cell, whose corrected H is >=
+// carry + e).  d_j is still folded into the next E, so per register-cell the
+// corrected pass drops one ALU max and E's update needs no space conversion.
 #pragma once
 #include "sw_batch.cuh"
 
@@ -44,7 +54,14 @@ struct LaneQ16 : LaneI16x2 {
 // (lo of a, lo of b) -> (a.lo, b.lo)
 __device__ __forceinline__ uint32_t lo_lo(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5410); }
 
-template <int L, int S>
+// Profile bias of the split kernel: o when D0 (h-space = X-space), else 128.
+template <bool D0>
+__host__ __device__ __forceinline__ int split_pb(int o)
+{
+    return D0 ? o : LaneQ16::PB;
+}
+
+template <int L, int S, bool D0>
 // len: this group's reference length; ncols: the warp's longest (every
 // lane runs ncols columns, columns past len use the inert residue)
 __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8_t *ref, int64_t start, int len,
@@ -58,7 +75,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int V = 4;
 
-    const LT::K k = LT::consts(o, e, S, one);
+    const LT::K k = LT::consts_pb(o, e, S, one, split_pb<D0>(o));
     T negW[LOGL];
 #pragma unroll
     for (int i = 0; i < LOGL; ++i)
@@ -118,14 +135,27 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 for (int j = 0; j < S; ++j) {
                     if (j % V == 0)
                         LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
-                    const T Ej = LT::max2(E[j], d);
-                    const T h = LT::h_of(hd, Pv[j % V], Ej, k);
-                    hd = LT::xd_corr(X[j], d, k);
-                    d = LT::dstep(d, k);
-                    const T ho = LT::ho_of(h, k);
-                    X[j] = LT::addmax(F, k.negO, ho);
-                    E[j] = LT::e_next(Ej, X[j], k);
-                    F = LT::addmax(F, k.negE, ho);
+                    T h;
+                    if constexpr (D0) {
+                        // d_j is dominated by the raised diagonal in h and
+                        // enters only the next E: max(E - e, d_j - e, X)
+                        h = LT::h_of(hd, Pv[j % V], E[j], k);
+                        hd = LT::max2(X[j], d);
+                        d = LT::dstep(d, k);
+                        const T ho = LT::ho_of(h, k);
+                        X[j] = LT::addmax(F, k.negO, ho);
+                        E[j] = LT::max3(LT::fadd(E[j], k.negE32, k), d, X[j]);
+                        F = LT::addmax(F, k.negE, ho);
+                    } else {
+                        const T Ej = LT::max2(E[j], d);
+                        h = LT::h_of(hd, Pv[j % V], Ej, k);
+                        hd = LT::xd_corr(X[j], d, k);
+                        d = LT::dstep(d, k);
+                        const T ho = LT::ho_of(h, k);
+                        X[j] = LT::addmax(F, k.negO, ho);
+                        E[j] = LT::e_next(Ej, X[j], k);
+                        F = LT::addmax(F, k.negE, ho);
+                    }
                     if (j & 1)
                         mx = LT::max3(mx, hpair, h);
                     else if (j == S - 1)
@@ -142,7 +172,10 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                     hd = X[j];
                     const T ho = LT::ho_of(h, k);
                     X[j] = LT::addmax(F, k.negO, ho);
-                    E[j] = LT::e_next(E[j], X[j], k);
+                    if constexpr (D0)
+                        E[j] = LT::addmax(E[j], k.negE, X[j]);  // same space: max(E - e, X)
+                    else
+                        E[j] = LT::e_next(E[j], X[j], k);
                     F = LT::addmax(F, k.negE, ho);
                     if (j & 1)
                         mx = LT::max3(mx, hpair, h);
@@ -177,7 +210,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     return mx;
 }
 
-template <int L, int S>
+template <int L, int S, bool D0>
 __global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs p)
 {
     constexpr int G = 32 / L;
@@ -192,6 +225,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs
     const int8_t *gprof = p.prof + (size_t)p.chunk * p.A * 2 * QH;
     const int qbase = p.chunk * 2 * QH;
     const int total = (p.A + 1) * L * SP;
+    const int pb = split_pb<D0>(p.o);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int a = idx / (L * SP);
         const int rem = idx - a * (L * SP);
@@ -201,9 +235,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs
         if (a < p.A && j < S) {
             const int plo = l * S + j, phi = QH + l * S + j;
             if (qbase + plo < p.qlen)
-                lo = (int)gprof[(size_t)a * 2 * QH + plo] + LaneQ16::PB;
+                lo = (int)gprof[(size_t)a * 2 * QH + plo] + pb;
             if (qbase + phi < p.qlen)
-                hi = (int)gprof[(size_t)a * 2 * QH + phi] + LaneQ16::PB;
+                hi = (int)gprof[(size_t)a * 2 * QH + phi] + pb;
         }
         sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] = (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
     }
@@ -215,7 +249,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs
     const int64_t n_work = p.n_work_dev ? (int64_t)(*p.n_work_dev) : p.n_work;
     const bool has_prev = p.chunk > 0;
     const bool has_next = p.chunk + 1 < p.nchunks;
-    const LaneQ16::K k = LaneQ16::consts(p.o, p.e, S, p.one);
+    const LaneQ16::K k = LaneQ16::consts_pb(p.o, p.e, S, p.one, split_pb<D0>(p.o));
 
     for (;;) {
         unsigned int ubase = 0;
@@ -230,7 +264,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs
         const int64_t start = seq[0] >= 0 ? p.off[seq[0]] : 0;
         const int len = seq[0] >= 0 ? (int)(p.off[seq[0] + 1] - start) : 0;
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
-        const uint32_t mx = split_unit<L, S>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one, has_prev,
+        const uint32_t mx = split_unit<L, S, D0>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one, has_prev,
                                              has_next, p.bnd, gl);
         if (gl == 0)
             write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);

@@ -96,6 +96,30 @@ def test_random_gap_costs(sw, kind):
         np.testing.assert_array_equal(got, want, err_msg="o=%d e=%d" % (o, e))
 
 
+@pytest.mark.parametrize("kind", ["i32", "i16x2", "i16x2q", "auto"])
+def test_both_corrected_passes(sw, kind):
+    """The scan-F kernels take a shorter corrected pass when the smallest
+    substitution score allows it (>= -(o+e) for int32 lanes, >= -o for
+    s16x2 lanes) and the general pass otherwise: mismatch scores on both
+    sides of both boundaries, several e, query-side insertions across many
+    segments and multi-chunk queries."""
+    rng = np.random.default_rng(1010)
+    queries, refs = gap_adversary(rng, 4, 24, ylo=60, yhi=400)
+    refs += [synth.residues(rng, int(n), 4) for n in (1, 5, 300, 2500)]
+    db, off = pack_list(refs)
+    db_d, off_d = db_to_dev(db, off)
+    queries = queries[:4] + [synth.residues(rng, n, 4) for n in (70, 700, 2100)]
+    for o in (3, 5):
+        for e in (0, 1, o):
+            for mm in sorted({-(o + e + 1), -(o + e), -(o + 1), -o, -o + 1}):
+                M = synth.dna_matrix(match=2, mismatch=mm)
+                for q in queries:
+                    want = oracle.gotoh_batch(q, db, off, M, o, e)
+                    got = run(sw, kind, q, M, db_d, off_d, o, e)
+                    np.testing.assert_array_equal(got, want, err_msg="o=%d e=%d mismatch=%d m=%d"
+                                                  % (o, e, mm, len(q)))
+
+
 @pytest.mark.parametrize("kind", LANES)
 def test_overflow_boundaries_rescored_exactly(sw, kind):
     """Identical DNA stretches whose true score sits just below, at and above
@@ -249,6 +273,24 @@ def test_pairs_gap_adversary(sw, kind):
     want = oracle.gotoh_pairs(q, q_off, r, r_off, M, 6, 1)
     got = run_pairs(sw, kind, q, q_off, r, r_off, M, 6, 1)
     np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", ["i32", "i16x2"])
+def test_pairs_both_corrected_passes(sw, kind):
+    """Pairs with mismatch scores on both sides of the shorter corrected
+    pass's conditions (>= -(o+e) int32, >= -o s16x2)."""
+    rng = np.random.default_rng(1104)
+    queries, refs = gap_adversary(rng, 4, 120, xlo=20, xhi=120, ylo=40, yhi=300)
+    queries = [x[:512] for x in queries]
+    q, q_off = pack_list(queries)
+    r, r_off = pack_list(refs)
+    o = 4
+    for e in (0, 1, 4):
+        for mm in sorted({-(o + e + 1), -(o + e), -(o + 1), -o, -o + 1}):
+            M = synth.dna_matrix(match=2, mismatch=mm)
+            want = oracle.gotoh_pairs(q, q_off, r, r_off, M, o, e)
+            got = run_pairs(sw, kind, q, q_off, r, r_off, M, o, e)
+            np.testing.assert_array_equal(got, want, err_msg="e=%d mismatch=%d" % (e, mm))
 
 
 def test_lazyf_pairs_exact_and_counts_steps(sw):
