@@ -22,7 +22,7 @@ CANDIDATES = {
                        (32, 32)),
     sw.SW_LANE_I32: ((4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 32)),
     # split-query s16x2: virtual lanes (two per thread)
-    sw.SW_LANE_I16X2Q: ((16, 8), (32, 8), (64, 8), (64, 16), (64, 32)),
+    sw.SW_LANE_I16X2Q: ((16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (64, 20), (64, 24), (64, 32)),
 }
 
 

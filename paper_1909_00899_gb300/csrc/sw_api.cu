@@ -105,11 +105,15 @@ const Choice kAllI32[] = {{4, 8},  {8, 8},   {8, 16},  {16, 8},  {16, 16}, {32, 
                           {32, 12}, {32, 16}, {8, 32},  {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
+const Choice kAllQ16[] = {{16, 8}, {32, 8}, {32, 16}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 32}};
 
 bool plan_supported(int lane, int L, int S)
 {
-    const Choice *t = lane == SW_LANE_I32 ? kAllI32 : (lane == SW_LANE_I16X2 ? kAllI16 : lane == SW_LANE_I8X4 ? kAllI8 : kQ16);
-    const int n = lane == SW_LANE_I32 ? 11 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 5);
+    const Choice *t = lane == SW_LANE_I32     ? kAllI32
+                      : lane == SW_LANE_I16X2 ? kAllI16
+                      : lane == SW_LANE_I8X4  ? kAllI8
+                                              : kAllQ16;
+    const int n = lane == SW_LANE_I32 ? 11 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 8);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;

@@ -49,8 +49,11 @@ int launch_batch_q16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream
                   : launch_split_inst<VL / 2, SS, false>(a, num_sms, st);
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
+    SWG_CASE(32, 16)
     SWG_CASE(64, 8)
     SWG_CASE(64, 16)
+    SWG_CASE(64, 20)
+    SWG_CASE(64, 24)
     SWG_CASE(64, 32)
 #undef SWG_CASE
     return (int)cudaErrorInvalidValue;
