@@ -127,18 +127,22 @@ const Choice kPairI8[] = {{8, 16}, {16, 10}, {16, 16}, {32, 16}};
 const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4;
 
 // Automatic choice of lane type and layout: the layout maximising
-// (useful positions / chunk positions) x its measured rate on GB300
-// (GCUPS, 100k log-normal protein sequences; refined per workload by the
-// autotuner).
+// its measured single-chunk rate on GB300 (GCUPS per processed cell, 100k
+// log-normal protein sequences; refined per workload by the autotuner)
+// x (useful positions / chunk positions) / (1 + 1.5 % per extra chunk: each
+// chunk launch re-streams the database, hands boundary rows on and drains
+// its own tail).
 struct AutoChoice {
     int lane, L, S;
     double gcups;
 };
 const AutoChoice kAuto[] = {
-    {SW_LANE_I16X2, 8, 8, 1400},    {SW_LANE_I16X2Q, 16, 8, 1900},  {SW_LANE_I16X2Q, 32, 8, 3000},
-    {SW_LANE_I16X2, 32, 16, 3670},  {SW_LANE_I16X2Q, 64, 8, 3370},  {SW_LANE_I16X2Q, 64, 16, 4100},
-    {SW_LANE_I16X2, 32, 32, 3870},  {SW_LANE_I16X2Q, 64, 32, 4350},
+    {SW_LANE_I16X2Q, 16, 8, 1964},  {SW_LANE_I16X2Q, 32, 8, 3443},  {SW_LANE_I16X2Q, 32, 16, 4257},
+    {SW_LANE_I16X2Q, 64, 8, 3956},  {SW_LANE_I16X2Q, 64, 16, 4808}, {SW_LANE_I16X2Q, 64, 20, 5030},
+    {SW_LANE_I16X2Q, 64, 24, 5030}, {SW_LANE_I16X2Q, 64, 32, 5130}, {SW_LANE_I16X2, 32, 16, 3865},
+    {SW_LANE_I16X2, 32, 32, 4578},
 };
+constexpr double kChunkCost = 0.015;
 
 Plan choose_auto(int32_t qlen)
 {
@@ -147,7 +151,8 @@ Plan choose_auto(int32_t qlen)
     for (const AutoChoice &c : kAuto) {
         const int QC = c.L * c.S;
         const int C = qlen > 0 ? (qlen + QC - 1) / QC : 1;
-        const double rate = c.gcups * (double)std::max(qlen, 1) / ((double)C * QC);
+        const double rate =
+            c.gcups * (double)std::max(qlen, 1) / ((double)C * QC) / (1.0 + kChunkCost * (double)(C - 1));
         if (rate > best_rate) {
             best_rate = rate;
             best.lane = c.lane;

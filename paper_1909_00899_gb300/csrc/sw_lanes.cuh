@@ -153,7 +153,7 @@ struct LaneI16x2 {
         uint32_t one;
         int bh;
         T negO, negE, delta, negDelta, xzero, hzero, xinit;
-        T hshift32, negE32, d0c32, negOS1_32;
+        T hshift32, negE32, d0c32, negOS1_32, cpos32;
     };
     // per-half constant for the DPX forms (saturated to 16 bits)
     __device__ __forceinline__ static T splat(int v)
@@ -182,6 +182,7 @@ struct LaneI16x2 {
         k.negE32 = splat32(-e);
         k.d0c32 = splat32(k.bh - BX - o);       // carry (X) -> d (h): c - o
         k.negOS1_32 = splat32(-o - (S - 1) * e);
+        k.cpos32 = splat32(0x7fff - BX);        // half > BX  <=>  bit 15 of half + 0x7fff - BX
         return k;
     }
     __device__ __forceinline__ static T fadd(T a, T b, const K &k) { return fadd_u32(a, k.one, b); }
@@ -201,9 +202,11 @@ struct LaneI16x2 {
     __device__ __forceinline__ static T d0_of(T c, const K &k) { return fadd(c, k.d0c32, k); }
     __device__ __forceinline__ static T dstep(T d, const K &k) { return fadd(d, k.negE32, k); }
     __device__ __forceinline__ static T xd_corr(T X, T d, const K &k) { return __viaddmax_s16x2(d, k.negDelta, X); }
-    __device__ __forceinline__ static bool carry_pos(T c, const K &)
+    // a positive carry in either half (halves are in [0, 0x7fff]; the sum
+    // stays below 0x10000, so no carry crosses into the high half)
+    __device__ __forceinline__ static bool carry_pos(T c, const K &k)
     {
-        return (int)(c & 0xffffu) > BX || (int)(c >> 16) > BX;
+        return (fadd(c, k.cpos32, k) & 0x80008000u) != 0u;
     }
     __device__ __forceinline__ static T last_corr(T X, T c, const K &k)
     {

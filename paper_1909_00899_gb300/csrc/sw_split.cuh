@@ -51,9 +51,6 @@ struct LaneQ16 : LaneI16x2 {
     }
 };
 
-// (lo of a, lo of b) -> (a.lo, b.lo)
-__device__ __forceinline__ uint32_t lo_lo(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5410); }
-
 // Profile bias of the split kernel: o when D0 (h-space = X-space), else 128.
 template <bool D0>
 __host__ __device__ __forceinline__ int split_pb(int o)
@@ -94,15 +91,26 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     }
     T c_prev = k.xzero;
     T hlast = k.xinit;
-    T hb_lo = k.xinit;  // previous chunk's last X at the previous column (low half used)
+    const uint32_t xinit16 = (uint32_t)(LT::BX - o);
+    uint32_t hb16 = xinit16;  // previous chunk's last X at the previous column (16 bits, lane 0)
     T mx = k.hzero;
+    // run-time 65536: the half-word moves below stay IMADs on the FMA pipe
+    const uint32_t m16 = one << 16;
+    const int rot = (gl + L - 1) & (L - 1);  // source lane of the diagonal
 
     for (int r0 = 0; r0 < ncols; r0 += L) {
         const int r = r0 + gl;
         const int myres = r < len ? min((int)ref[start + r], A) : A;
-        int2 mybnd = make_int2(-o, 0);
-        if (has_prev && r < len)
-            mybnd = bnd[start + r];
+        // this lane's column of the boundary row written by the previous
+        // chunk (raw packed values; their high halves belong to that chunk's
+        // last position), converted once here: its X as a 16-bit value and
+        // the F entering as the pair (F, 0)
+        uint32_t my_h16 = xinit16, my_f = k.xzero;
+        if (has_prev && r < len) {
+            const uint2 raw = reinterpret_cast<const uint2 *>(bnd)[start + r];
+            my_h16 = raw.x >> 16;
+            my_f = __byte_perm(raw.y, k.xzero, 0x5432);
+        }
         const int cols = min(L, ncols - r0);
         for (int rr = 0; rr < cols; ++rr) {
             const int rc = r0 + rr;
@@ -110,23 +118,23 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
             res[0] = __shfl_sync(FULL, myres, rr, L);
             T Pv[V];
 
-            // diagonal: lane l-1's last values; lane 0 takes the chunk
-            // boundary (low) and lane L-1's last low half (high)
-            const T up = __shfl_up_sync(FULL, hlast, 1, L);
-            const T last = __shfl_sync(FULL, hlast, L - 1, L);
-            T hd = up;
+            // diagonal: lane l-1's last values (one rotated shuffle); lane 0
+            // takes the chunk boundary (low half) and lane L-1's last low
+            // half (high half)
+            const T v = __shfl_sync(FULL, hlast, rot, L);
+            T hd = v;
             T F = k.xzero;
-            T lo_in = k.xinit;
+            uint32_t lo_in = xinit16;
             if (has_prev) {
-                const int bh = __shfl_sync(FULL, mybnd.x, rr, L);
-                const int bf = __shfl_sync(FULL, mybnd.y, rr, L);
-                lo_in = hb_lo;
-                hb_lo = (uint32_t)((bh + LT::BX) & 0xffff) * 0x10001u;
+                const uint32_t bh = __shfl_sync(FULL, my_h16, rr, L);
+                const uint32_t bf = __shfl_sync(FULL, my_f, rr, L);
+                lo_in = hb16;
+                hb16 = bh;
                 if (gl == 0)
-                    F = lo_lo((uint32_t)((bf + LT::BX) & 0xffff), k.xzero);
+                    F = bf;
             }
             if (gl == 0)
-                hd = lo_lo(lo_in, last);
+                hd = fadd_u32(v, m16, lo_in);  // (lo_in, low half of v)
 
             T hpair = k.hzero;
             if (__any_sync(FULL, LT::carry_pos(c_prev, k))) {
@@ -194,14 +202,15 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 x = LT::addmax(y, negW[i], x);
             }
             const T gb = __shfl_sync(FULL, x, L - 1, L);
-            x = LT::addmax(lo_lo(neg_lo, gb), wfold, x);
+            x = LT::addmax(fadd_u32(gb, m16, neg_lo), wfold, x);  // (-32768, low half of gb) + fold
             T cin = __shfl_up_sync(FULL, x, 1, L);
             if (gl == 0)
-                cin = lo_lo(k.xzero, gb);
+                cin = fadd_u32(gb, m16, (uint32_t)LT::BX);  // (0, low half of gb)
             c_prev = cin;
             hlast = LT::last_corr(X[S - 1], cin, k);
+            // the next chunk reads the high halves (this chunk's last position)
             if (has_next && gl == L - 1 && rc < len)
-                bnd[start + rc] = make_int2(LT::x_true(hlast, 1), LT::x_true(x, 1));
+                reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, x);
         }
     }
 #pragma unroll
@@ -210,8 +219,17 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     return mx;
 }
 
+// CTAs of 256 threads per SM the register budget is held to (48, 64, 80 or
+// 128 registers a thread), the most each segment length fits without spills
+// (short segments serve short queries, which are latency-bound and want the
+// extra warps)
+template <int S, bool D0>
+struct SplitMinBlocks {
+    static constexpr int value = D0 ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2) : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
+};
+
 template <int L, int S, bool D0>
-__global__ void __launch_bounds__(BATCH_THREADS) sw_split_kernel(const BatchArgs p)
+__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) sw_split_kernel(const BatchArgs p)
 {
     constexpr int G = 32 / L;
     constexpr int SP = SegPad<S, 4>::value;
