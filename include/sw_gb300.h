@@ -16,9 +16,10 @@
  * from the query).  Scores are exact int32 whatever lane type computes them.
  *
  * Conventions for every call
- *  - Residues are codes 0..A-1 in uint8.  A database code >= A is read as
- *    an unknown residue that never scores (its column cannot raise H
- *    through a match); query codes >= A are rejected by sw_profile_build.
+ *  - Residues are codes 0..A-1 in uint8.  A code >= A (in a database
+ *    sequence, or in a query of sw_align_pairs) is an unknown residue: it
+ *    scores the smallest entry of the substitution matrix against anything,
+ *    on every lane type.  sw_profile_build rejects query codes >= A.
  *  - "device" pointers are CUDA device memory on the current device, owned
  *    by the caller; "host" pointers are host memory owned by the caller and
  *    only read during the call.

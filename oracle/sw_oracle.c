@@ -30,7 +30,10 @@
  *
  * Conventions: residues are codes 0..A-1; the substitution matrix M is A*A,
  * row-major, indexed M[query residue][reference residue] (the query profile
- * of Alg. 1 is built from the query, so the query picks the row).
+ * of Alg. 1 is built from the query, so the query picks the row).  A code
+ * >= A on either side is an unknown residue and scores the smallest entry of
+ * M against anything (the paper has no such residues; this is the library's
+ * convention, the same for every lane type).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -40,6 +43,22 @@
 #define NEG_INF (INT32_MIN / 4)
 
 static inline int32_t imax(int32_t a, int32_t b) { return a > b ? a : b; }
+
+/* smallest entry of M: the score of an unknown residue (code >= A) */
+static int32_t min_entry(const int8_t *M, int32_t A)
+{
+    int32_t v = 127;
+    for (int32_t i = 0; i < A * A; ++i)
+        if (M[i] < v)
+            v = M[i];
+    return v;
+}
+
+/* M[qc][rc], or the smallest entry when either code is outside 0..A-1 */
+static inline int32_t subst(const int8_t *M, int32_t A, int32_t minM, int32_t qc, int32_t rc)
+{
+    return (qc < A && rc < A) ? (int32_t)M[qc * A + rc] : minM;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Textbook Gotoh, int32.  Rows are query positions q = 1..m, columns are    */
@@ -55,6 +74,7 @@ int32_t oracle_gotoh(const uint8_t *query, int32_t m, const uint8_t *ref,
 {
     if (m <= 0 || n <= 0)
         return 0;
+    const int32_t minM = min_entry(M, A);
     int32_t *Hcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t *Ecol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
     for (int32_t q = 0; q <= m; ++q) {
@@ -70,7 +90,7 @@ int32_t oracle_gotoh(const uint8_t *query, int32_t m, const uint8_t *ref,
         for (int32_t q = 1; q <= m; ++q) {
             const int32_t Eq = imax(Hcol[q] - o, Ecol[q] - e);
             const int32_t Fq = imax(up - o, F - e);
-            int32_t H = diag + (int32_t)M[query[q - 1] * A + rc];
+            int32_t H = diag + subst(M, A, minM, query[q - 1], rc);
             H = imax(H, Eq);
             H = imax(H, Fq);
             H = imax(H, 0);
@@ -101,6 +121,7 @@ int32_t oracle_gotoh_end(const uint8_t *query, int32_t m, const uint8_t *ref,
     *r_end = -1;
     if (m <= 0 || n <= 0)
         return 0;
+    const int32_t minM = min_entry(M, A);
     int32_t *Hcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t *Ecol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
     for (int32_t q = 0; q <= m; ++q) {
@@ -114,7 +135,7 @@ int32_t oracle_gotoh_end(const uint8_t *query, int32_t m, const uint8_t *ref,
         for (int32_t q = 1; q <= m; ++q) {
             const int32_t Eq = imax(Hcol[q] - o, Ecol[q] - e);
             const int32_t Fq = imax(up - o, F - e);
-            int32_t H = diag + (int32_t)M[query[q - 1] * A + rc];
+            int32_t H = diag + subst(M, A, minM, query[q - 1], rc);
             H = imax(imax(imax(H, Eq), Fq), 0);
             diag = Hcol[q];
             Hcol[q] = H;
@@ -144,6 +165,7 @@ typedef struct {
     const uint8_t *q, *r;
     int32_t m, n, A, o, e;
     const int8_t *M;
+    int32_t minM;
     int32_t best;
     int32_t best_q, best_r; /* end cell of the best path (1-based), first in column order */
 } brute_ctx;
@@ -165,7 +187,7 @@ static void brute_walk(brute_ctx *c, int32_t i, int32_t j, int32_t last,
         c->best_r = j;
     }
     if (i < c->m && j < c->n)
-        brute_walk(c, i + 1, j + 1, 0, score + c->M[c->q[i] * c->A + c->r[j]]);
+        brute_walk(c, i + 1, j + 1, 0, score + subst(c->M, c->A, c->minM, c->q[i], c->r[j]));
     if (i < c->m)
         brute_walk(c, i + 1, j, 1, score - (last == 1 ? c->e : c->o));
     if (j < c->n)
@@ -186,7 +208,7 @@ int32_t oracle_brute(const uint8_t *query, int32_t m, const uint8_t *ref,
                      int32_t n, const int8_t *M, int32_t A, int32_t o,
                      int32_t e)
 {
-    brute_ctx c = {query, ref, m, n, A, o, e, M, 0, -1, -1};
+    brute_ctx c = {query, ref, m, n, A, o, e, M, min_entry(M, A), 0, -1, -1};
     return brute_run(&c);
 }
 
@@ -195,7 +217,7 @@ int32_t oracle_brute_end(const uint8_t *query, int32_t m, const uint8_t *ref,
                          int32_t n, const int8_t *M, int32_t A, int32_t o,
                          int32_t e, int32_t *q_end, int32_t *r_end)
 {
-    brute_ctx c = {query, ref, m, n, A, o, e, M, 0, -1, -1};
+    brute_ctx c = {query, ref, m, n, A, o, e, M, min_entry(M, A), 0, -1, -1};
     const int32_t s = brute_run(&c);
     *q_end = s > 0 ? c.best_q : -1;
     *r_end = s > 0 ? c.best_r : -1;
@@ -212,18 +234,20 @@ int32_t oracle_brute_end(const uint8_t *query, int32_t m, const uint8_t *ref,
 static inline int32_t sat_sub(int32_t a, int32_t b) { return imax(a - b, 0); }
 
 /* vprofile[c][j][lane]: score of query position lane*segLen+j against      */
-/* residue c.  Positions past the query end get a score that keeps them at  */
-/* 0 after flooring (they can never raise Max).                             */
+/* residue c, c = 0..A (row A: an unknown residue).  Positions past the     */
+/* query end get a score that keeps them at 0 after flooring (they can      */
+/* never raise Max).                                                        */
 static int32_t *build_vprofile(const uint8_t *query, int32_t m, const int8_t *M,
                                int32_t A, int32_t p, int32_t segLen)
 {
-    int32_t *vp = (int32_t *)malloc(sizeof(int32_t) * (size_t)A * segLen * p);
-    for (int32_t c = 0; c < A; ++c)
+    const int32_t minM = min_entry(M, A);
+    int32_t *vp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A + 1) * segLen * p);
+    for (int32_t c = 0; c <= A; ++c)
         for (int32_t j = 0; j < segLen; ++j)
             for (int32_t l = 0; l < p; ++l) {
                 const int32_t pos = l * segLen + j;
                 vp[((size_t)c * segLen + j) * p + l] =
-                    pos < m ? (int32_t)M[query[pos] * A + c] : NEG_INF;
+                    pos < m ? subst(M, A, minM, query[pos], c) : NEG_INF;
             }
     return vp;
 }
@@ -270,7 +294,7 @@ int32_t oracle_striped_lazyf(const uint8_t *query, int32_t m,
     int64_t steps = 0;
 
     for (int32_t i = 0; i < n; ++i) {
-        const int32_t *vp = vprofile + (size_t)ref[i] * segLen * p;
+        const int32_t *vp = vprofile + (size_t)(ref[i] < A ? ref[i] : A) * segLen * p;
         for (int32_t l = 0; l < p; ++l)
             F[l] = 0;
         vshift(H, HStore + (size_t)(segLen - 1) * p, p);
@@ -366,7 +390,7 @@ int32_t oracle_striped_scan(const uint8_t *query, int32_t m, const uint8_t *ref,
     int32_t Max = 0;
 
     for (int32_t i = 0; i < n; ++i) {
-        const int32_t *vp = vprofile + (size_t)ref[i] * segLen * p;
+        const int32_t *vp = vprofile + (size_t)(ref[i] < A ? ref[i] : A) * segLen * p;
         for (int32_t l = 0; l < p; ++l) {
             F[l] = 0;
             carryNew[l] = 0;

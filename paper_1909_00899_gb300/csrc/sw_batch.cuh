@@ -100,8 +100,9 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
 #pragma unroll
         for (int c = 0; c < CELLS; ++c) {
             const int r = r0 + gl;
-            // codes >= A read as the inert row A (never out of the staged profile)
-            myres[c] = r < len[c] ? min((int)ref[start[c] + r], A) : A;
+            // codes >= A read as the unknown-residue row A; columns past the
+            // sequence end read the inert row A+1
+            myres[c] = r < len[c] ? min((int)ref[start[c] + r], A) : A + 1;
             mybnd[c] = make_int2(-o, 0);
             if (has_prev && r < len[c])
                 mybnd[c] = bnd[start[c] + r];
@@ -334,23 +335,24 @@ __device__ __forceinline__ void write_scores(typename LT::T mx, const typename L
 
 // Stage one striped profile (biased by the lane type's profile bias) into
 // shared memory in the layout load_profile reads: [residue][SP/VEC][lane][VEC].
-// value(a, l, j) gives the raw score of residue a at lane l, segment index j
-// (j < S) or a sentinel below -256 for positions past the query end; row A
-// is inert.
+// value(a, l, j) gives the raw score of residue a (0..A, row A: an unknown
+// residue, scored as the smallest matrix entry) at lane l, segment index j
+// (j < S), or a sentinel below -256 for positions past the query end; row
+// A+1 is inert (columns past a sequence's end).
 template <class LT, int L, int S, class ValueFn>
 __device__ __forceinline__ void stage_profile(typename LT::Elem *dst, int A, int o, int tid, int nthreads,
                                               ValueFn value)
 {
     constexpr int V = LT::VEC;
     constexpr int SP = SegPad<S, V>::value;
-    const int total = (A + 1) * L * SP;
+    const int total = (A + 2) * L * SP;
     for (int idx = tid; idx < total; idx += nthreads) {
         const int a = idx / (L * SP);
         const int rem = idx - a * (L * SP);
         const int l = rem / SP;
         const int j = rem - l * SP;
         int v = LT::PAD;
-        if (a < A && j < S) {
+        if (a <= A && j < S) {
             const int raw = value(a, l, j);
             if (raw > -256)
                 v = raw + LT::prof_bias(o);
@@ -378,7 +380,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
     const int qbase = p.chunk * QC;
     const int qlen = p.qlen;
     stage_profile<LT, L, S>(sprof, p.A, p.o, threadIdx.x, blockDim.x, [&](int a, int l, int j) {
-        return qbase + l * S + j < qlen ? (int)gprof[(size_t)a * QC + l * S + j] : -1024;
+        if (qbase + l * S + j >= qlen)
+            return -1024;
+        return a < p.A ? (int)gprof[(size_t)a * QC + l * S + j] : (int)p.min_m;
     });
     __syncthreads();
 

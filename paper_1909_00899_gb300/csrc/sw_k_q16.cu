@@ -12,7 +12,7 @@ template <int L, int S, bool D0>
 static int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
     auto kern = sw_split_kernel<L, S, D0>;
-    constexpr size_t kMaxSmem = (size_t)33 * L * SegPad<S, 4>::value * 4;
+    constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, 4>::value * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -20,7 +20,7 @@ static int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
     });
     if (attr_err != cudaSuccess)
         return (int)attr_err;
-    const size_t smem = (size_t)(a.A + 1) * L * SegPad<S, 4>::value * 4;
+    const size_t smem = (size_t)(a.A + 2) * L * SegPad<S, 4>::value * 4;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem);
     if (err != cudaSuccess)

@@ -10,7 +10,8 @@ template <class LT, int L, int S, bool LAZY, bool ENDS = false>
 int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
     auto kern = sw_batch_kernel<LT, L, S, LAZY, ENDS>;
-    constexpr size_t kMaxSmem = (size_t)33 * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
+    // alphabet of at most 32 residues + the unknown and the inert rows
+    constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -18,7 +19,7 @@ int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
     });
     if (attr_err != cudaSuccess)
         return (int)attr_err;
-    const size_t smem = (size_t)(a.A + 1) * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
+    const size_t smem = (size_t)(a.A + 2) * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem);
     if (err != cudaSuccess)

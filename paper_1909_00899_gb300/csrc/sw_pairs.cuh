@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int A = p.A;
-    const int cell_elems = (A + 1) * L * SP;
+    const int cell_elems = (A + 2) * L * SP;  // rows 0..A-1, unknown residue A, inert A+1
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int grp = lane / L;
@@ -78,17 +78,13 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
                 const int l = pos / SP;
                 const int j = pos - l * SP;
                 const int qp = l * S + j;
-                int code = -1;
-                if (j < S && qp < ql) {
-                    code = (int)p.q[qs + qp];
-                    if (code >= A)
-                        code = -1;  // unknown query residue: never scores
-                }
+                // query code (>= A: an unknown residue), -1 past the query end
+                const int code = (j < S && qp < ql) ? (int)p.q[qs + qp] : -1;
 #pragma unroll 4
-                for (int a = 0; a <= A; ++a) {
+                for (int a = 0; a <= A + 1; ++a) {
                     int v = LT::PAD;
-                    if (code >= 0 && a < A)
-                        v = (int)p.M[code * A + a] + LT::prof_bias(p.o);
+                    if (code >= 0 && a <= A)
+                        v = (code < A && a < A ? (int)p.M[code * A + a] : (int)p.min_m) + LT::prof_bias(p.o);
                     dst[((a * (SP / V) + j / V) * L + l) * V + (j % V)] = (Elem)v;
                 }
             }
@@ -110,7 +106,7 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
 template <class LT, int S>
 constexpr size_t pair_smem_per_warp(int A)
 {
-    return (size_t)32 * LT::CELLS * (A + 1) * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
+    return (size_t)32 * LT::CELLS * (A + 2) * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
 }
 
 template <class LT, int L, int S, bool LAZY>

@@ -100,7 +100,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
 
     for (int r0 = 0; r0 < ncols; r0 += L) {
         const int r = r0 + gl;
-        const int myres = r < len ? min((int)ref[start + r], A) : A;
+        const int myres = r < len ? min((int)ref[start + r], A) : A + 1;  // unknown row A, inert row A+1
         // this lane's column of the boundary row written by the previous
         // chunk (raw packed values; their high halves belong to that chunk's
         // last position), converted once here: its X as a 16-bit value and
@@ -239,10 +239,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) s
     uint32_t *sprof = reinterpret_cast<uint32_t *>(smem_raw);
 
     // stage the chunk: raw profile of 2L virtual lanes [A][2L][S]; pair
-    // virtual lanes l and L + l into one 32-bit element
+    // virtual lanes l and L + l into one 32-bit element.  Row A: an unknown
+    // residue (the smallest matrix entry); row A+1: inert
     const int8_t *gprof = p.prof + (size_t)p.chunk * p.A * 2 * QH;
     const int qbase = p.chunk * 2 * QH;
-    const int total = (p.A + 1) * L * SP;
+    const int total = (p.A + 2) * L * SP;
     const int pb = split_pb<D0>(p.o);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int a = idx / (L * SP);
@@ -250,12 +251,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) s
         const int l = rem / SP;
         const int j = rem - l * SP;
         int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
-        if (a < p.A && j < S) {
+        if (a <= p.A && j < S) {
             const int plo = l * S + j, phi = QH + l * S + j;
             if (qbase + plo < p.qlen)
-                lo = (int)gprof[(size_t)a * 2 * QH + plo] + pb;
+                lo = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + plo] : (int)p.min_m) + pb;
             if (qbase + phi < p.qlen)
-                hi = (int)gprof[(size_t)a * 2 * QH + phi] + pb;
+                hi = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + phi] : (int)p.min_m) + pb;
         }
         sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] = (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
     }

@@ -121,6 +121,28 @@ def test_both_corrected_passes(sw, kind):
 
 
 @pytest.mark.parametrize("kind", LANES)
+def test_unknown_database_residues(sw, kind):
+    """Database codes >= A score the smallest matrix entry on every lane
+    type (the oracle's convention): DNA and protein matrices, both sides of
+    the shorter corrected pass's condition, one- and multi-chunk queries."""
+    rng = np.random.default_rng(1011)
+    for M, o, e in ((synth.dna_matrix(match=2, mismatch=-3), 5, 1),
+                    (synth.dna_matrix(match=2, mismatch=-3), 2, 1),
+                    (synth.protein_matrix(rng), 11, 1)):
+        A = M.shape[0]
+        lens = np.concatenate([[1, 3], rng.integers(20, 900, 60)]).astype(np.int64)
+        db, off = synth.pack(lens, rng, A)
+        hit = rng.random(len(db)) < 0.08
+        db[hit] = rng.choice(np.array([A, A + 1, 255], np.uint8), int(hit.sum()))
+        db_d, off_d = db_to_dev(db, off)
+        for qlen in (150, 700, 2300):
+            q = synth.residues(rng, qlen, A)
+            want = oracle.gotoh_batch(q, db, off, M, o, e)
+            got = run(sw, kind, q, M, db_d, off_d, o, e)
+            np.testing.assert_array_equal(got, want, err_msg="A=%d o=%d m=%d" % (A, o, qlen))
+
+
+@pytest.mark.parametrize("kind", LANES)
 def test_overflow_boundaries_rescored_exactly(sw, kind):
     """Identical DNA stretches whose true score sits just below, at and above
     the s8 (127) and s16 (32767) ceilings: packed lanes must flag them and
@@ -291,6 +313,25 @@ def test_pairs_both_corrected_passes(sw, kind):
             want = oracle.gotoh_pairs(q, q_off, r, r_off, M, o, e)
             got = run_pairs(sw, kind, q, q_off, r, r_off, M, o, e)
             np.testing.assert_array_equal(got, want, err_msg="e=%d mismatch=%d" % (e, mm))
+
+
+@pytest.mark.parametrize("kind", PAIR_LANES)
+def test_pairs_unknown_residues(sw, kind):
+    """Codes >= A in the reads and in the windows score the smallest matrix
+    entry, as in the oracle."""
+    rng = np.random.default_rng(1105)
+    M = synth.dna_matrix(match=2, mismatch=-3)
+    qlens = rng.integers(1, 400, 300).astype(np.int64)
+    rlens = rng.integers(1, 900, 300).astype(np.int64)
+    q, q_off = synth.pack(qlens, rng, 4)
+    r, r_off = synth.pack(rlens, rng, 4)
+    for s in (q, r):
+        hit = rng.random(len(s)) < 0.05
+        s[hit] = rng.choice(np.array([4, 5, 255], np.uint8), int(hit.sum()))
+    for o, e in ((5, 1), (2, 2)):
+        want = oracle.gotoh_pairs(q, q_off, r, r_off, M, o, e)
+        got = run_pairs(sw, kind, q, q_off, r, r_off, M, o, e)
+        np.testing.assert_array_equal(got, want, err_msg="o=%d e=%d" % (o, e))
 
 
 def test_lazyf_pairs_exact_and_counts_steps(sw):

@@ -252,3 +252,53 @@ def test_end_batch_matches_single():
     s, qe, re_ = oracle.gotoh_end_batch(q, db, off, M, 11, 1, nthreads=3)
     for k in range(40):
         assert (s[k], qe[k], re_[k]) == oracle.gotoh_end(q, db[off[k]:off[k + 1]], M, 11, 1)
+
+
+def _extend_alphabet(q, r, M):
+    """Codes >= A mapped to one extra code A whose row and column hold the
+    smallest entry of M: the unknown-residue convention as a plain
+    (A+1)-letter problem, with no code outside the extended alphabet."""
+    A = M.shape[0]
+    Mx = np.full((A + 1, A + 1), M.min(), dtype=np.int8)
+    Mx[:A, :A] = M
+    return np.minimum(q, A).astype(np.uint8), np.minimum(r, A).astype(np.uint8), Mx
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_unknown_residues_score_the_smallest_entry(seed):
+    """A code >= A on either side scores min(M) against anything: the same
+    as an extra alphabet letter with that row and column (checked by the
+    recurrence and, on tiny inputs, by enumeration), and identical in the
+    striped variants."""
+    rng = np.random.default_rng(600 + seed)
+    M = synth.dna_matrix(match=2, mismatch=-3) if seed % 2 == 0 else synth.protein_matrix(rng)
+    A = M.shape[0]
+    unk = np.array([A, A + 1, 200, 255], dtype=np.uint8)
+    for _ in range(30):
+        q = synth.residues(rng, int(rng.integers(1, 40)), A)
+        r = synth.residues(rng, int(rng.integers(1, 60)), A)
+        for s in (q, r):
+            k = rng.integers(0, len(s) // 3 + 1)
+            s[rng.integers(0, len(s), k)] = rng.choice(unk, k)
+        qx, rx, Mx = _extend_alphabet(q, r, M)
+        for o, e in ((5, 1), (3, 3), (11, 1)):
+            want = oracle.gotoh(qx, rx, Mx, o, e)
+            assert oracle.gotoh(q, r, M, o, e) == want
+            assert oracle.striped_scan(q, r, M, o, e, 4) == want
+            assert oracle.striped_lazyf(q, r, M, o, e, 4) == want
+            assert oracle.gotoh_end(q, r, M, o, e) == oracle.gotoh_end(qx, rx, Mx, o, e)
+    for _ in range(40):
+        q = rng.integers(0, A + 2, int(rng.integers(1, 7))).astype(np.uint8)
+        r = rng.integers(0, A + 2, int(rng.integers(1, 7))).astype(np.uint8)
+        qx, rx, Mx = _extend_alphabet(q, r, M)
+        assert oracle.gotoh(q, r, M, 4, 1) == oracle.brute(qx, rx, Mx, 4, 1)
+
+
+def test_unknown_residue_all_positive_matrix():
+    """With a matrix of only positive entries an unknown residue still
+    scores min(M) > 0 and extends the alignment (it is a residue, not a
+    gap or a stop)."""
+    M = np.array([[3, 1], [1, 2]], dtype=np.int8)
+    q = np.array([0, 9, 1], dtype=np.uint8)
+    r = np.array([0, 0, 1], dtype=np.uint8)
+    assert oracle.gotoh(q, r, M, 5, 1) == 3 + 1 + 2
