@@ -162,9 +162,34 @@ def cpu_baseline_oracle(w, qlens, target_s):
         oracle.gotoh_batch(q, sub_db, sub_off, w["M"], w["o"], w["e"], nthreads=cores)
         cells += len(q) * int(lens[ids].sum())
     dt = time.perf_counter() - t0
+    # one core on a slice of the same sample
+    ids1 = ids[:: max(1, cores)]
+    sub1, off1 = _subset(w["db"], off, ids1)
+    t1 = time.perf_counter()
+    cells1 = 0
+    for q in w["queries"]:
+        oracle.gotoh_batch(q, sub1, off1, w["M"], w["o"], w["e"], nthreads=1)
+        cells1 += len(q) * int(lens[ids1].sum())
+    dt1 = time.perf_counter() - t1
+    # the CPU striped variants (informative): Alg. 6 scan and Alg. 1 lazy-F
+    # with p = 8 lanes, one thread, the second query against a few sequences
+    striped = {}
+    q = w["queries"][min(1, len(w["queries"]) - 1)]
+    for name, fn in (("scan", oracle.striped_scan), ("lazyf", oracle.striped_lazyf)):
+        t2, c2, k = time.perf_counter(), 0, 0
+        while time.perf_counter() - t2 < 1.5 and k < n:
+            i = ids[k % len(ids)]
+            fn(q, w["db"][off[i]:off[i + 1]], w["M"], w["o"], w["e"], 8)
+            c2 += len(q) * int(lens[i])
+            k += 1
+        striped[name] = c2 / (time.perf_counter() - t2) / 1e9
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
             "sample": "all %d queries vs every %d-th db sequence (%d seqs, %.3g cells, %.1f s)"
-                      % (len(w["queries"]), step, len(ids), cells, dt)}
+                      % (len(w["queries"]), step, len(ids), cells, dt),
+            "single_core": {"value": cells1 / dt1 / 1e9, "unit": "GCUPS", "cores": 1,
+                            "sample": "every %d-th of those sequences" % max(1, cores)},
+            "striped_p8_one_core": {"scan_gcups": striped["scan"], "lazyf_gcups": striped["lazyf"],
+                                    "sample": "query m=%d vs the first sampled sequences, ~1.5 s each" % len(q)}}
 
 
 def _subset(db, off, ids):
@@ -520,7 +545,8 @@ def run_pairs(args):
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     res = {}
-    for name, lane in (("s16x2", sw.SW_LANE_I16X2), ("s8x4", sw.SW_LANE_I8X4), ("int32", sw.SW_LANE_I32)):
+    for name, lane in (("s16x2_split", sw.SW_LANE_I16X2Q), ("s16x2", sw.SW_LANE_I16X2), ("s8x4", sw.SW_LANE_I8X4),
+                       ("int32", sw.SW_LANE_I32)):
         fn = lambda: sw.sw_align_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, lane_type=lane, stream=st)
         for _ in range(args.warmup):
             fn()

@@ -193,8 +193,10 @@ int sw_align_lazyf_db(const sw_profile *prof, const sw_db *db,
  *   q, r            device residue codes;  q_off, r_off  device int64[n+1]
  *   subst_matrix    host, alphabet*alphabet int8 [query][reference]
  *                   (copied into the launch parameters)
- *   lane_type       SW_LANE_*: packed types flag pairs whose score may have
- *                   left the lane range and rescore them in int32
+ *   lane_type       SW_LANE_* (SW_LANE_I16X2Q: one pair per group, the two
+ *                   query halves in the two halves of each register);
+ *                   packed types flag pairs whose score may have left the
+ *                   lane range and rescore them in int32
  *   scores_out      device int32[n_pairs]
  * Query lengths up to 512 per pair (SW_ERR_RANGE otherwise).  Pairs are
  * sorted into query-length classes on the device; the class sizes are read

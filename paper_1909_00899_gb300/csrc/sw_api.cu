@@ -124,7 +124,8 @@ bool plan_supported(int lane, int L, int S)
 const Choice kPairI32[] = {{4, 8}, {8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
 const Choice kPairI16[] = {{8, 8}, {16, 8}, {16, 10}, {32, 8}, {32, 16}};
 const Choice kPairI8[] = {{8, 16}, {16, 10}, {16, 16}, {32, 16}};
-const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4;
+const Choice kPairQ16[] = {{16, 8}, {16, 10}, {32, 8}, {32, 12}, {32, 16}};  // virtual lanes
+const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4, kPairQ16N = 5;
 
 // Automatic choice of lane type and layout: the layout maximising
 // its measured single-chunk rate on GB300 (GCUPS per processed cell, 100k
@@ -692,8 +693,8 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
         return fail(SW_ERR_INVALID, "subst_matrix is NULL");
     if (alphabet < 1 || alphabet > 32)
         return fail(SW_ERR_INVALID, "alphabet must be in 1..32 (got %d)", alphabet);
-    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I8X4)
-        return fail(SW_ERR_INVALID, "pairs take lane types AUTO, I32, I16X2 or I8X4 (got %d)", lane_type);
+    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I16X2Q)
+        return fail(SW_ERR_INVALID, "pairs take lane types AUTO, I32, I16X2, I8X4 or I16X2Q (got %d)", lane_type);
     if (gap_open < 1)
         return fail(SW_ERR_INVALID, "gap_open must be >= 1 (got %d)", gap_open);
     if (gap_extend < 0 || gap_extend > gap_open)
@@ -715,7 +716,9 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
     a.min_m = minM;
     sw_profile shape;  // only the matrix range is read by lane_fits
     shape.maxM = maxM;
-    int lane = lazy ? SW_LANE_I32 : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2 : lane_type);
+    // automatic: split s16x2 (one pair per group, no byte permutes), measured
+    // fastest on reads vs windows
+    int lane = lazy ? SW_LANE_I32 : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2Q : lane_type);
     // query-length classes of the lane type; the packed classes must fit
     const Choice *tab = kPairI32;
     int ncls = kPairI32N;
@@ -725,6 +728,9 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
     } else if (lane == SW_LANE_I8X4) {
         tab = kPairI8;
         ncls = kPairI8N;
+    } else if (lane == SW_LANE_I16X2Q) {
+        tab = kPairQ16;
+        ncls = kPairQ16N;
     }
     if (lane != SW_LANE_I32) {
         Plan widest;
@@ -800,7 +806,10 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
             continue;
         const int32_t *cls = order + begin;
         a.counter = counters + 2 * k;
-        const int lk = lane == SW_LANE_I32 ? swg::LK_I32 : (lane == SW_LANE_I16X2 ? swg::LK_I16X2 : swg::LK_I8X4);
+        const int lk = lane == SW_LANE_I32     ? swg::LK_I32
+                       : lane == SW_LANE_I16X2 ? swg::LK_I16X2
+                       : lane == SW_LANE_I8X4  ? swg::LK_I8X4
+                                               : swg::LK_I16X2Q;
         a.flag_thresh = thresh;
         kr = swg::launch_pairs(lk, tab[k].L, tab[k].S, lazy, a, cls, nullptr, cnt, sms, st);
         if (kr)

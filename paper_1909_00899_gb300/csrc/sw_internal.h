@@ -6,7 +6,7 @@
 
 namespace swg {
 
-enum LaneKind { LK_I32 = 1, LK_I16X2 = 2, LK_I8X4 = 3 };
+enum LaneKind { LK_I32 = 1, LK_I16X2 = 2, LK_I8X4 = 3, LK_I16X2Q = 4 };
 
 // One layout of the striped query: L lanes per alignment, S positions per
 // lane (the paper's p and segLen), C query chunks of L*S positions each.

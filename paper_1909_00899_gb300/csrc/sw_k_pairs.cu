@@ -1,4 +1,5 @@
-// Pair-kernel instantiations: query-length classes per lane type.
+// Pair-kernel instantiations: query-length classes per lane type (the split
+// s16x2 classes count virtual lanes, two per thread).
 #include <algorithm>
 
 #include "sw_pairs.cuh"
@@ -37,6 +38,18 @@ int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int
         SWG_CASE16(16, 10)
         SWG_CASE16(32, 8)
         SWG_CASE16(32, 16)
+    } else if (lane == LK_I16X2Q) {
+        // virtual lanes (two per thread), as the batch split layouts
+#define SWG_CASEQ(VL, SS)                                                                                        \
+    if (L == VL && S == SS)                                                                                      \
+        return d0_16 ? launch_pairs_split_inst<VL / 2, SS, true>(a, list, count_dev, n_hint, num_sms, st)       \
+                     : launch_pairs_split_inst<VL / 2, SS, false>(a, list, count_dev, n_hint, num_sms, st);
+        SWG_CASEQ(16, 8)
+        SWG_CASEQ(16, 10)
+        SWG_CASEQ(32, 8)
+        SWG_CASEQ(32, 12)
+        SWG_CASEQ(32, 16)
+#undef SWG_CASEQ
     } else if (lane == LK_I8X4) {
         SWG_CASE(LaneI8x4, 8, 16)
         SWG_CASE(LaneI8x4, 16, 10)

@@ -8,6 +8,7 @@
 // positions (single chunk).
 #pragma once
 #include "sw_batch.cuh"
+#include "sw_split.cuh"
 
 namespace swg {
 
@@ -132,6 +133,111 @@ int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *cou
     const int64_t units = (n_hint + LT::CELLS - 1) / LT::CELLS;
     const int64_t per_block = (int64_t)warps * (32 / L);
     const int64_t need = (units + per_block - 1) / per_block;
+    if (need < grid)
+        grid = need;
+    if (grid < 1)
+        return (int)cudaSuccess;
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(a, list, count_dev, n_hint);
+    return (int)cudaGetLastError();
+}
+
+// Split-query s16x2 pair kernel: a group of L threads takes one pair and
+// holds the first half of its query in the low halves and the second half
+// in the high halves (2L virtual lanes, sw_split.cuh); each group stages its
+// pair's profile as (low position, high position) pairs in its own slice of
+// shared memory, row A the unknown residue, row A+1 inert.
+template <int L, int S, bool D0>
+__global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, const int32_t *__restrict__ list,
+                                                             const int32_t *__restrict__ count_dev, int64_t n_list)
+{
+    constexpr int SP = SegPad<S, 4>::value;
+    constexpr int QH = L * S;  // positions per half
+    constexpr int G = 32 / L;
+    constexpr unsigned FULL = 0xffffffffu;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int A = p.A;
+    const int cell_elems = (A + 2) * L * SP;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const int gid = (threadIdx.x >> 5) * G + grp;
+    uint32_t *gprof = reinterpret_cast<uint32_t *>(smem_raw) + (size_t)gid * cell_elems;
+    const int pb = split_pb<D0>(p.o);
+    const LaneQ16::K k = LaneQ16::consts_pb(p.o, p.e, S, p.one, pb);
+    const int64_t n_work = count_dev ? (int64_t)(*count_dev) : n_list;
+
+    for (;;) {
+        unsigned int ubase = 0;
+        if (lane == 0)
+            ubase = atomicAdd(p.counter, (unsigned int)G);
+        ubase = __shfl_sync(FULL, ubase, 0);
+        if ((int64_t)ubase >= n_work)
+            break;
+        const int64_t w = (int64_t)ubase + grp;
+        int pid[1];
+        pid[0] = w < n_work ? (list ? list[w] : (int)w) : -1;
+        int64_t qs = 0, start = 0;
+        int ql = 0, len = 0;
+        if (pid[0] >= 0) {
+            qs = p.q_off[pid[0]];
+            ql = (int)(p.q_off[pid[0] + 1] - qs);
+            start = p.r_off[pid[0]];
+            len = (int)(p.r_off[pid[0] + 1] - start);
+        }
+        if (ql == 0)
+            len = 0;  // empty query: score 0
+        for (int pos = gl; pos < L * SP; pos += L) {
+            const int l = pos / SP;
+            const int j = pos - l * SP;
+            const int plo = l * S + j, phi = QH + l * S + j;
+            // query codes (>= A: an unknown residue), -1 past the query end
+            const int clo = (j < S && plo < ql) ? (int)p.q[qs + plo] : -1;
+            const int chi = (j < S && phi < ql) ? (int)p.q[qs + phi] : -1;
+            for (int a = 0; a <= A + 1; ++a) {
+                int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
+                if (a <= A) {
+                    if (clo >= 0)
+                        lo = (clo < A && a < A ? (int)p.M[clo * A + a] : (int)p.min_m) + pb;
+                    if (chi >= 0)
+                        hi = (chi < A && a < A ? (int)p.M[chi * A + a] : (int)p.min_m) + pb;
+                }
+                gprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] =
+                    (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+            }
+        }
+        __syncwarp(FULL);
+        const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
+        const uint32_t mx =
+            split_unit<L, S, D0>(gprof, p.r, start, len, ncols, A, p.o, p.e, p.one, false, false, nullptr, gl);
+        if (gl == 0)
+            write_scores<LaneQ16>(mx, k, pid, false, p.flag_thresh, p.scores);
+        __syncwarp(FULL);  // the profile is rewritten by the next unit
+    }
+}
+
+template <int L, int S, bool D0>
+int launch_pairs_split_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
+                            int num_sms, cudaStream_t st)
+{
+    auto kern = sw_pairs_split_kernel<L, S, D0>;
+    const size_t per_warp = (size_t)32 * (a.A + 2) * SegPad<S, 4>::value * 4;
+    int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
+    const size_t smem = per_warp * warps;
+    if (smem > 200 * 1024)
+        return (int)cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return (int)err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (err != cudaSuccess)
+        return (int)err;
+    if (per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    const int64_t per_block = (int64_t)warps * (32 / L);
+    const int64_t need = (n_hint + per_block - 1) / per_block;
     if (need < grid)
         grid = need;
     if (grid < 1)

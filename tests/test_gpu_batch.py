@@ -231,12 +231,12 @@ def test_cell_rate_probe_runs(sw):
 # sw_align_pairs: each pair with its own query
 # ---------------------------------------------------------------------------
 
-PAIR_LANES = ["i32", "i16x2", "i8x4", "auto"]
+PAIR_LANES = ["i32", "i16x2", "i16x2q", "i8x4", "auto"]
 
 
 def run_pairs(sw, kind, q, q_off, r, r_off, M, o, e):
-    lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i8x4": sw.SW_LANE_I8X4,
-            "auto": sw.SW_LANE_AUTO}[kind]
+    lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i16x2q": sw.SW_LANE_I16X2Q,
+            "i8x4": sw.SW_LANE_I8X4, "auto": sw.SW_LANE_AUTO}[kind]
     qd, qo = db_to_dev(q, q_off)
     rd, ro = db_to_dev(r, r_off)
     n = len(q_off) - 1
@@ -297,7 +297,7 @@ def test_pairs_gap_adversary(sw, kind):
     np.testing.assert_array_equal(got, want)
 
 
-@pytest.mark.parametrize("kind", ["i32", "i16x2"])
+@pytest.mark.parametrize("kind", ["i32", "i16x2", "i16x2q"])
 def test_pairs_both_corrected_passes(sw, kind):
     """Pairs with mismatch scores on both sides of the shorter corrected
     pass's conditions (>= -(o+e) int32, >= -o s16x2)."""
