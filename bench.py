@@ -271,7 +271,7 @@ def main():
     side = [torch.cuda.Stream() for _ in range(max(1, args.streams))]
 
     def lazy_lane(lazy):
-        return sw.SW_LANE_I16X2 if lazy == "s16x2" else sw.SW_LANE_I32
+        return {"s16x2": sw.SW_LANE_I16X2, "s16x2_split": sw.SW_LANE_I16X2Q}.get(lazy, sw.SW_LANE_I32)
 
     def step(lazy=False):
         """One pass of the path: every query's profile and its alignment
@@ -349,7 +349,7 @@ def main():
     if not args.no_lazyf:
         lsteps = max(1, min(args.steps, 2))
         by_lane = {}
-        for lz in ("int32", "s16x2"):
+        for lz in ("int32", "s16x2", "s16x2_split"):
             lms = timed(lsteps, lazy=lz)
             lper = per_query(lazy=lz)
             by_lane[lz] = {"value": cells_step * lsteps / (lms * 1e-3) / 1e9, "unit": "GCUPS",

@@ -156,9 +156,10 @@ int sw_align_batch_ends(const sw_profile *prof, const uint8_t *db_residues,
  * sw_align_lazyf_batch — same inputs, outputs and errors as sw_align_batch,
  * computed with the lazy-F correction loop of Alg. 1 (up to p rounds of
  * shift-and-correct per column, leaving as soon as no lane's carried F can
- * raise anything).  Runs on the profile's layout when it is int32 or
- * two-alignment s16x2 (flagged s16x2 alignments are rescored with the
- * scan-F int32 kernel), on the int32 layout otherwise.  The comparison.
+ * raise anything).  Runs on the profile's own layout: int32, two-alignment
+ * s16x2 or split s16x2 (the latter with up to 2p rounds over its 2p virtual
+ * lanes; flagged s16x2 alignments are rescored with the scan-F int32
+ * kernel); an s8x4 profile runs on the int32 layout.  The comparison.
  */
 int sw_align_lazyf_batch(const sw_profile *prof, const uint8_t *db_residues,
                          const int64_t *db_offsets, int64_t n_db,

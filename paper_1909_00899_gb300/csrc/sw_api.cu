@@ -19,7 +19,7 @@ namespace swg {
 int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i16(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
-int launch_batch_q16(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_q16(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 }  // namespace swg
 
@@ -270,7 +270,7 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
     if (pl.lane == SW_LANE_I16X2)
         return swg::launch_batch_i16(pl, lazy, a, sms, st);
     if (pl.lane == SW_LANE_I16X2Q)
-        return swg::launch_batch_q16(pl, a, sms, st);
+        return swg::launch_batch_q16(pl, lazy, a, sms, st);
     return swg::launch_batch_i8(pl, a, sms, st);
 }
 
@@ -306,9 +306,10 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     keep_pool_warm(dev);
     const int sms = num_sms_of(dev);
 
-    // lazy-F runs on the profile's int32 or two-alignment s16x2 layout
+    // lazy-F runs on the profile's own layout (int32, two-alignment or split
+    // s16x2; s8x4 profiles fall back to int32)
     int lane = ends ? SW_LANE_I32 : prof->lane;
-    if (lazy && lane != SW_LANE_I16X2)
+    if (lazy && lane == SW_LANE_I8X4)
         lane = SW_LANE_I32;
     if (lane != SW_LANE_I32 && !lane_fits(lane, prof, o, e, prof->plan))
         lane = SW_LANE_I32;  // values do not fit the packed lanes: exact int32 throughout

@@ -58,12 +58,15 @@ __host__ __device__ __forceinline__ int split_pb(int o)
     return D0 ? o : LaneQ16::PB;
 }
 
-template <int L, int S, bool D0>
+template <int L, int S, bool D0, bool LAZY = false>
 // len: this group's reference length; ncols: the warp's longest (every
-// lane runs ncols columns, columns past len use the inert residue)
+// lane runs ncols columns, columns past len use the inert residue).
+// LAZY: the lazy-F loop of Alg. 1 over the 2L virtual lanes instead of the
+// scan (the comparison kernel); lazy_steps counts its j-steps.
 __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8_t *ref, int64_t start, int len,
                                                int ncols, int A, int o, int e, uint32_t one, bool has_prev,
-                                               bool has_next, int2 *bnd, int gl)
+                                               bool has_next, int2 *bnd, int gl,
+                                               unsigned long long *lazy_steps = nullptr)
 {
     using LT = LaneQ16;
     using T = uint32_t;
@@ -137,7 +140,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 hd = fadd_u32(v, m16, lo_in);  // (lo_in, low half of v)
 
             T hpair = k.hzero;
-            if (__any_sync(FULL, LT::carry_pos(c_prev, k))) {
+            if (!LAZY && __any_sync(FULL, LT::carry_pos(c_prev, k))) {
                 T d = LT::d0_of(c_prev, k);
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
@@ -193,24 +196,62 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                         hpair = h;
                 }
             }
-            // scan of both halves at once, then the first half's outgoing F
-            // (low half of lane L-1) folded into the second half
-            T x = F;
+            if constexpr (LAZY) {
+                // lazy-F (Alg. 1): shift the F leaving each virtual lane into
+                // the next one (lane L-1's low half into lane 0's high half)
+                // and correct, for at most 2L rounds; leave every round once
+                // no lane's carried F can raise anything (reading R6)
+                T fb = F;  // F leaving this lane, corrected as rounds pass
+                T Fc = __shfl_sync(FULL, F, rot, L);
+                if (gl == 0)
+                    Fc = fadd_u32(Fc, m16, (uint32_t)LT::BX);  // (0, low half of lane L-1)
+                bool done = false;
+                unsigned long long steps = 0;
+                for (int kk = 0; kk < 2 * L && !done; ++kk) {
 #pragma unroll
-            for (int i = 0; i < LOGL; ++i) {
-                const T y = __shfl_up_sync(FULL, x, 1 << i, L);
-                x = LT::addmax(y, negW[i], x);
+                    for (int j = 0; j < S; ++j) {
+                        const T hold = X[j];
+                        X[j] = LT::addmax(Fc, k.negO, hold);
+                        E[j] = LT::e_raise(E[j], X[j], k);
+                        Fc = LT::lazy_step(Fc, k);
+                        ++steps;
+                        if (__all_sync(FULL, LT::lazy_dominated(Fc, hold, k))) {
+                            done = true;
+                            break;
+                        }
+                    }
+                    if (!done) {
+                        fb = LT::max2(fb, Fc);
+                        Fc = __shfl_sync(FULL, Fc, rot, L);
+                        if (gl == 0)
+                            Fc = fadd_u32(Fc, m16, (uint32_t)LT::BX);
+                    }
+                }
+                if (lazy_steps)
+                    *lazy_steps += steps;
+                hlast = X[S - 1];
+                if (has_next && gl == L - 1 && rc < len)
+                    reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, fb);
+            } else {
+                // scan of both halves at once, then the first half's outgoing
+                // F (low half of lane L-1) folded into the second half
+                T x = F;
+#pragma unroll
+                for (int i = 0; i < LOGL; ++i) {
+                    const T y = __shfl_up_sync(FULL, x, 1 << i, L);
+                    x = LT::addmax(y, negW[i], x);
+                }
+                const T gb = __shfl_sync(FULL, x, L - 1, L);
+                x = LT::addmax(fadd_u32(gb, m16, neg_lo), wfold, x);  // (-32768, low half of gb) + fold
+                T cin = __shfl_up_sync(FULL, x, 1, L);
+                if (gl == 0)
+                    cin = fadd_u32(gb, m16, (uint32_t)LT::BX);  // (0, low half of gb)
+                c_prev = cin;
+                hlast = LT::last_corr(X[S - 1], cin, k);
+                // the next chunk reads the high halves (this chunk's last position)
+                if (has_next && gl == L - 1 && rc < len)
+                    reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, x);
             }
-            const T gb = __shfl_sync(FULL, x, L - 1, L);
-            x = LT::addmax(fadd_u32(gb, m16, neg_lo), wfold, x);  // (-32768, low half of gb) + fold
-            T cin = __shfl_up_sync(FULL, x, 1, L);
-            if (gl == 0)
-                cin = fadd_u32(gb, m16, (uint32_t)LT::BX);  // (0, low half of gb)
-            c_prev = cin;
-            hlast = LT::last_corr(X[S - 1], cin, k);
-            // the next chunk reads the high halves (this chunk's last position)
-            if (has_next && gl == L - 1 && rc < len)
-                reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, x);
         }
     }
 #pragma unroll
@@ -228,7 +269,7 @@ struct SplitMinBlocks {
     static constexpr int value = D0 ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2) : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
 };
 
-template <int L, int S, bool D0>
+template <int L, int S, bool D0, bool LAZY = false>
 __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) sw_split_kernel(const BatchArgs p)
 {
     constexpr int G = 32 / L;
@@ -269,6 +310,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) s
     const bool has_prev = p.chunk > 0;
     const bool has_next = p.chunk + 1 < p.nchunks;
     const LaneQ16::K k = LaneQ16::consts_pb(p.o, p.e, S, p.one, split_pb<D0>(p.o));
+    unsigned long long lazy_steps = 0;
 
     for (;;) {
         unsigned int ubase = 0;
@@ -283,11 +325,14 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) s
         const int64_t start = seq[0] >= 0 ? p.off[seq[0]] : 0;
         const int len = seq[0] >= 0 ? (int)(p.off[seq[0] + 1] - start) : 0;
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
-        const uint32_t mx = split_unit<L, S, D0>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one, has_prev,
-                                             has_next, p.bnd, gl);
+        const uint32_t mx = split_unit<L, S, D0, LAZY>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
+                                                       has_prev, has_next, p.bnd, gl, &lazy_steps);
         if (gl == 0)
             write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);
     }
+    // j-steps of the correction loop, counted once per warp
+    if (LAZY && p.lazy_steps && lane == 0 && lazy_steps)
+        atomicAdd(p.lazy_steps, lazy_steps);
 }
 
 }  // namespace swg

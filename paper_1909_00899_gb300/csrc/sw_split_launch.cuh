@@ -1,0 +1,63 @@
+// Launch helper of the split-query s16x2 kernels (scan-F and lazy-F
+// translation units).
+#pragma once
+#include <mutex>
+
+#include "sw_split.cuh"
+
+namespace swg {
+
+template <int L, int S, bool D0, bool LAZY>
+int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
+{
+    auto kern = sw_split_kernel<L, S, D0, LAZY>;
+    constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, 4>::value * 4;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    });
+    if (attr_err != cudaSuccess)
+        return (int)attr_err;
+    const size_t smem = (size_t)(a.A + 2) * L * SegPad<S, 4>::value * 4;
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem);
+    if (err != cudaSuccess)
+        return (int)err;
+    if (per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (!a.n_work_dev) {
+        const int64_t per_block = (BATCH_THREADS / 32) * (32 / L);
+        const int64_t need = (a.n_work + per_block - 1) / per_block;
+        if (need < grid)
+            grid = need;
+    }
+    if (grid < 1)
+        return (int)cudaSuccess;
+    kern<<<(unsigned)grid, BATCH_THREADS, smem, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+// the layouts (virtual lanes, two per thread) and both passes of one method
+template <bool LAZY>
+int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
+{
+    const bool d0 = a.min_m >= -a.o;
+#define SWG_CASE(VL, SS)                                                                     \
+    if (pl.L == VL && pl.S == SS)                                                            \
+        return d0 ? launch_split_inst<VL / 2, SS, true, LAZY>(a, num_sms, st)                \
+                  : launch_split_inst<VL / 2, SS, false, LAZY>(a, num_sms, st);
+    SWG_CASE(16, 8)
+    SWG_CASE(32, 8)
+    SWG_CASE(32, 16)
+    SWG_CASE(64, 8)
+    SWG_CASE(64, 16)
+    SWG_CASE(64, 20)
+    SWG_CASE(64, 24)
+    SWG_CASE(64, 32)
+#undef SWG_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace swg

@@ -77,6 +77,12 @@ def test_every_compiled_layout_is_exact(sw, small_db, lane):
             sw.sw_align_batch(prof, db_d, off_d, 11, 1, out)
             torch.cuda.synchronize()
             np.testing.assert_array_equal(out.cpu().numpy(), want, err_msg="lane %d L=%d S=%d m=%d" % (lane, L, S, m))
+            if lane in (1, 2, 4):  # lazy-F runs on these layouts too
+                out.fill_(-7)
+                sw.sw_align_lazyf_batch(prof, db_d, off_d, 11, 1, out)
+                torch.cuda.synchronize()
+                np.testing.assert_array_equal(out.cpu().numpy(), want,
+                                              err_msg="lazy-F lane %d L=%d S=%d m=%d" % (lane, L, S, m))
             prof.free()
 
 

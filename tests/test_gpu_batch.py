@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-LANES = ["i32", "i16x2", "i16x2q", "i8x4", "auto", "lazyf", "lazyf16"]
+LANES = ["i32", "i16x2", "i16x2q", "i8x4", "auto", "lazyf", "lazyf16", "lazyf16q"]
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +27,7 @@ def sw():
 def run(sw, kind, query, M, db_d, off_d, o, e):
     lane = {"i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2, "i16x2q": sw.SW_LANE_I16X2Q,
             "i8x4": sw.SW_LANE_I8X4, "auto": sw.SW_LANE_AUTO, "lazyf": sw.SW_LANE_I32,
-            "lazyf16": sw.SW_LANE_I16X2}[kind]
+            "lazyf16": sw.SW_LANE_I16X2, "lazyf16q": sw.SW_LANE_I16X2Q}[kind]
     prof = sw.Profile(query, M, lane)
     n = off_d.numel() - 1
     out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
@@ -96,7 +96,7 @@ def test_random_gap_costs(sw, kind):
         np.testing.assert_array_equal(got, want, err_msg="o=%d e=%d" % (o, e))
 
 
-@pytest.mark.parametrize("kind", ["i32", "i16x2", "i16x2q", "auto"])
+@pytest.mark.parametrize("kind", ["i32", "i16x2", "i16x2q", "auto", "lazyf16q"])
 def test_both_corrected_passes(sw, kind):
     """The scan-F kernels take a shorter corrected pass when the smallest
     substitution score allows it (>= -(o+e) for int32 lanes, >= -o for
