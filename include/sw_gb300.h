@@ -116,6 +116,14 @@ int sw_profile_free_async(sw_profile *prof, void *cuda_stream);
 int sw_profile_plan(const sw_profile *prof, int32_t *lanes, int32_t *seg_len,
                     int32_t *chunks, int32_t *lane_type);
 
+/* The plan sw_profile_build would choose for a query of qlen residues and
+ * lane_type (SW_LANE_AUTO: the layout maximising the measured single-chunk
+ * rate x useful positions / chunk positions, less 1.5 % per extra chunk),
+ * without building anything: host only, no CUDA call.  Any out pointer may
+ * be NULL.  SW_ERR_INVALID for qlen < 0 or an unknown lane type. */
+int sw_plan_query(int32_t qlen, int32_t lane_type, int32_t *lanes,
+                  int32_t *seg_len, int32_t *chunks, int32_t *lane_out);
+
 /*
  * sw_align_batch — scores of one profiled query against n_db database
  * sequences with the scan-F method (Alg. 6): per reference column each lane

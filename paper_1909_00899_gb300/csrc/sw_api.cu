@@ -572,6 +572,25 @@ int sw_profile_plan(const sw_profile *prof, int32_t *lanes, int32_t *seg_len, in
     return SW_OK;
 }
 
+int sw_plan_query(int32_t qlen, int32_t lane_type, int32_t *lanes, int32_t *seg_len, int32_t *chunks,
+                  int32_t *lane_out)
+{
+    if (qlen < 0)
+        return fail(SW_ERR_INVALID, "qlen < 0 (%d)", qlen);
+    if (lane_type < SW_LANE_AUTO || lane_type > SW_LANE_I16X2Q)
+        return fail(SW_ERR_INVALID, "unknown lane type %d", lane_type);
+    const Plan pl = lane_type == SW_LANE_AUTO ? choose_auto(qlen) : choose_plan(qlen, lane_type);
+    if (lanes)
+        *lanes = pl.L;
+    if (seg_len)
+        *seg_len = pl.S;
+    if (chunks)
+        *chunks = pl.C;
+    if (lane_out)
+        *lane_out = pl.lane;
+    return SW_OK;
+}
+
 int sw_align_batch(const sw_profile *prof, const uint8_t *db_residues, const int64_t *db_offsets, int64_t n_db,
                    int32_t gap_open, int32_t gap_extend, int32_t *scores_out, void *cuda_stream)
 {

@@ -33,7 +33,7 @@ EXPORTS = (
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
-    "sw_align_batch_ends",
+    "sw_align_batch_ends", "sw_plan_query",
 )
 
 
@@ -67,6 +67,8 @@ def lib():
         L.sw_profile_free_async.argtypes = [_vp, _vp]
         L.sw_profile_plan.restype = ctypes.c_int
         L.sw_profile_plan.argtypes = [_vp] + [ctypes.POINTER(_i32)] * 4
+        L.sw_plan_query.restype = ctypes.c_int
+        L.sw_plan_query.argtypes = [_i32, _i32] + [ctypes.POINTER(_i32)] * 4
         for name in ("sw_align_batch", "sw_align_lazyf_batch", "sw_align_batch_noalloc"):
             f = getattr(L, name)
             f.restype = ctypes.c_int
@@ -324,6 +326,13 @@ def sw_align_lazyf_db_stats(profile, db, gap_open, gap_extend, scores_out, lazy_
     _check(lib().sw_align_lazyf_db_stats(profile.handle, db.handle, int(gap_open), int(gap_extend),
                                          _dev_ptr(scores_out, "int32"), steps, _stream(stream)))
     return scores_out
+
+
+def sw_plan_query(qlen, lane_type=SW_LANE_AUTO):
+    """The plan a profile of qlen residues would get (host only)."""
+    vals = [_i32() for _ in range(4)]
+    _check(lib().sw_plan_query(int(qlen), int(lane_type), *[ctypes.byref(v) for v in vals]))
+    return dict(lanes=vals[0].value, seg_len=vals[1].value, chunks=vals[2].value, lane_type=vals[3].value)
 
 
 def sw_stream_sync(stream=None, timeout_ms=60_000):

@@ -62,3 +62,28 @@ def test_invalid_arguments_rejected_without_cuda(swlib):
     assert L.sw_align_batch(None, None, None, 0, 11, 1, None, None) == swlib.SW_ERR_INVALID
     assert L.sw_align_lazyf_batch(None, None, None, 0, 11, 1, None, None) == swlib.SW_ERR_INVALID
     assert L.sw_probe_cell_rate(7, 10, None, None) == swlib.SW_ERR_INVALID
+
+
+def test_plan_query_covers_the_query_host_only(swlib):
+    """sw_plan_query (no CUDA call): every lane type's plan covers the query
+    with the fewest chunks of its layout; the automatic plan uses the split
+    s16x2 lanes, wastes under half a chunk for queries of 128+ residues and
+    picks the layouts the measured rates favour at the benchmark lengths."""
+    for lane in (0, 1, 2, 3, 4):
+        for m in (0, 1, 7, 64, 100, 128, 129, 300, 512, 777, 1024, 2048, 3000, 5000, 12345):
+            p = swlib.sw_plan_query(m, lane)
+            QC = p["lanes"] * p["seg_len"]
+            assert QC > 0
+            assert p["chunks"] == (m + QC - 1) // QC
+            assert p["lane_type"] == lane if lane else p["lane_type"] in (2, 4)
+            if lane == 0 and m >= 128:
+                assert m / (p["chunks"] * QC) > 0.5
+    picks = {m: swlib.sw_plan_query(m) for m in (128, 512, 2048, 5000)}
+    assert picks[128] == dict(lanes=16, seg_len=8, chunks=1, lane_type=4)
+    assert picks[512] == dict(lanes=32, seg_len=16, chunks=1, lane_type=4)
+    assert picks[2048] == dict(lanes=64, seg_len=32, chunks=1, lane_type=4)
+    assert picks[5000] == dict(lanes=64, seg_len=20, chunks=4, lane_type=4)
+    with pytest.raises(swlib.SwError):
+        swlib.sw_plan_query(-1)
+    with pytest.raises(swlib.SwError):
+        swlib.sw_plan_query(10, 9)
