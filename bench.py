@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--n-pairs", type=int, default=1_000_000)
     ap.add_argument("--n-queries", type=int, default=64, help="ragged: queries taken from the 10,000")
     ap.add_argument("--serve-db", type=int, default=1_000_000)
-    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--streams", type=int, default=4,
                     help="CUDA streams the independent queries of a step are spread over")
     return ap.parse_args()

@@ -60,7 +60,7 @@ __host__ __device__ __forceinline__ int split_pb(int o)
 
 template <int L, int S, bool D0, bool LAZY = false>
 // len: this group's reference length; ncols: the warp's longest (every
-// lane runs ncols columns, columns past len use the inert residue).
+// lane runs ncols columns, columns past len use the inert row A+1).
 // LAZY: the lazy-F loop of Alg. 1 over the 2L virtual lanes instead of the
 // scan (the comparison kernel); lazy_steps counts its j-steps.
 __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8_t *ref, int64_t start, int len,
