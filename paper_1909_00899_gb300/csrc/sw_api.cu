@@ -21,6 +21,7 @@ int launch_batch_i16(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
 int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_q16(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_q16_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 }  // namespace swg
 
 using swg::Plan;
@@ -276,7 +277,8 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
 
 // pre_order / pre_total: a database handle's persistent length order and
 // residue count (then no order kernels run and nothing is read back).
-// q_end / r_end: end cells wanted (int32 lanes, ENDS kernels)
+// q_end / r_end: end cells wanted (ENDS kernels: split s16x2 lanes for split
+// profiles, int32 lanes otherwise and for the rescore)
 int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, int64_t n_db, int32_t o, int32_t e,
                int32_t *scores, void *stream, bool lazy, const int32_t *pre_order = nullptr,
                int64_t pre_total = -1, unsigned long long *lazy_steps = nullptr, int32_t *q_end = nullptr,
@@ -308,8 +310,8 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
 
     // lazy-F runs on the profile's own layout (int32, two-alignment or split
     // s16x2; s8x4 profiles fall back to int32)
-    int lane = ends ? SW_LANE_I32 : prof->lane;
-    if (lazy && lane == SW_LANE_I8X4)
+    int lane = prof->lane;
+    if ((lazy && lane == SW_LANE_I8X4) || (ends && lane != SW_LANE_I16X2Q))
         lane = SW_LANE_I32;
     if (lane != SW_LANE_I32 && !lane_fits(lane, prof, o, e, prof->plan))
         lane = SW_LANE_I32;  // values do not fit the packed lanes: exact int32 throughout
@@ -386,7 +388,9 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     for (int c = 0; c < main.C; ++c) {
         a.chunk = c;
         a.counter = counters + c;
-        kr = ends ? swg::launch_batch_i32_ends(main, a, sms, st) : launch_plan(main, lazy, a, sms, st);
+        kr = !ends                    ? launch_plan(main, lazy, a, sms, st)
+             : lane == SW_LANE_I32    ? swg::launch_batch_i32_ends(main, a, sms, st)
+                                      : swg::launch_batch_q16_ends(main, a, sms, st);
         if (kr)
             return cuda_fail(kr, "batch kernel launch");
     }
@@ -403,7 +407,8 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
         for (int c = 0; c < C32; ++c) {
             a.chunk = c;
             a.counter = counters + main.C + c;
-            kr = launch_plan(prof->plan32, false, a, sms, st);
+            kr = ends ? swg::launch_batch_i32_ends(prof->plan32, a, sms, st)
+                      : launch_plan(prof->plan32, false, a, sms, st);
             if (kr)
                 return cuda_fail(kr, "rescore kernel launch");
         }

@@ -58,16 +58,29 @@ __host__ __device__ __forceinline__ int split_pb(int o)
     return D0 ? o : LaneQ16::PB;
 }
 
-template <int L, int S, bool D0, bool LAZY = false>
+template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false>
 // len: this group's reference length; ncols: the warp's longest (every
 // lane runs ncols columns, columns past len use the inert row A+1).
 // LAZY: the lazy-F loop of Alg. 1 over the 2L virtual lanes instead of the
 // scan (the comparison kernel); lazy_steps counts its j-steps.
+// ENDS (scan-F): also the group's end cell, the first cell in column order
+// whose h reaches the maximum, as end_r (0-based column) and end_q (0-based
+// position in the chunk), -1 when nothing scored above 0.  A lane half notes
+// the column in which its running maximum rose above the group's running
+// maximum (a few instructions per column; the group maximum is re-reduced
+// only in such columns) and recovers the row there from the stored X: within
+// a column the F a lane's pass starts from is 0 (every carry is deferred), so
+// F - o stays below the h - o of the column's best cell and X[j] == h - o of
+// the maximum holds exactly at the cells that reached it.  A half whose
+// maximum ends below the alignment's score may keep a stale note; it never
+// wins the final reduction.
 __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8_t *ref, int64_t start, int len,
                                                int ncols, int A, int o, int e, uint32_t one, bool has_prev,
                                                bool has_next, int2 *bnd, int gl,
-                                               unsigned long long *lazy_steps = nullptr)
+                                               unsigned long long *lazy_steps = nullptr, int *end_r = nullptr,
+                                               int *end_q = nullptr)
 {
+    static_assert(!(LAZY && ENDS), "end cells: scan-F only");
     using LT = LaneQ16;
     using T = uint32_t;
     constexpr int SP = SegPad<S, 4>::value;
@@ -100,6 +113,13 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     // run-time 65536: the half-word moves below stay IMADs on the FMA pipe
     const uint32_t m16 = one << 16;
     const int rot = (gl + L - 1) & (L - 1);  // source lane of the diagonal
+    // scan-F: the chunk boundary's F enters lane 0's low half as its carry,
+    // decaying by S*e through the segment (high half untouched)
+    const T wS = (uint32_t)((-S * e) & 0xffff);
+    // ENDS, per half: the column, segment index and h-space value of the
+    // half's last note (value 0: none)
+    int br_lo = -1, bj_lo = 0, bv_lo = 0, br_hi = -1, bj_hi = 0, bv_hi = 0;
+    T gm = k.hzero;  // ENDS: the group's running maximum (h-space, both halves; the zero score at first)
 
     for (int r0 = 0; r0 < ncols; r0 += L) {
         const int r = r0 + gl;
@@ -107,12 +127,13 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
         // this lane's column of the boundary row written by the previous
         // chunk (raw packed values; their high halves belong to that chunk's
         // last position), converted once here: its X as a 16-bit value and
-        // the F entering as the pair (F, 0)
-        uint32_t my_h16 = xinit16, my_f = k.xzero;
+        // the F entering (lazy-F: as the pair (F, 0) that starts lane 0's
+        // pass; scan-F: as a 16-bit carry)
+        uint32_t my_h16 = xinit16, my_f = LAZY ? k.xzero : (uint32_t)LT::BX;
         if (has_prev && r < len) {
             const uint2 raw = reinterpret_cast<const uint2 *>(bnd)[start + r];
             my_h16 = raw.x >> 16;
-            my_f = __byte_perm(raw.y, k.xzero, 0x5432);
+            my_f = LAZY ? __byte_perm(raw.y, k.xzero, 0x5432) : raw.y >> 16;
         }
         const int cols = min(L, ncols - r0);
         for (int rr = 0; rr < cols; ++rr) {
@@ -128,18 +149,24 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
             T hd = v;
             T F = k.xzero;
             uint32_t lo_in = xinit16;
+            uint32_t bf16 = (uint32_t)LT::BX;  // scan-F: the boundary F (16 bits), no carry by default
             if (has_prev) {
                 const uint32_t bh = __shfl_sync(FULL, my_h16, rr, L);
                 const uint32_t bf = __shfl_sync(FULL, my_f, rr, L);
                 lo_in = hb16;
                 hb16 = bh;
-                if (gl == 0)
-                    F = bf;
+                if (LAZY) {
+                    if (gl == 0)
+                        F = bf;
+                } else {
+                    bf16 = bf;
+                }
             }
             if (gl == 0)
                 hd = fadd_u32(v, m16, lo_in);  // (lo_in, low half of v)
 
             T hpair = k.hzero;
+            const T mx_start = mx;
             if (!LAZY && __any_sync(FULL, LT::carry_pos(c_prev, k))) {
                 T d = LT::d0_of(c_prev, k);
 #pragma unroll
@@ -196,6 +223,48 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                         hpair = h;
                 }
             }
+            if constexpr (ENDS) {
+                // Only a cell that raises the group's running maximum can be
+                // the end cell (a later cell that merely ties it comes after
+                // the one that set it), so the halves are looked at only in
+                // columns where some half rose above that maximum (gm); the
+                // group maximum is then re-reduced, and each half that rose
+                // to it notes the first cell (smallest j) whose X is h - o of
+                // the maximum.
+                const bool cand = mx != mx_start && LT::max2(mx, gm) != gm;
+                if (__any_sync(FULL, cand)) {
+                    int g = max((int)(mx & 0xffffu), (int)(mx >> 16));
+#pragma unroll
+                    for (int dd = L / 2; dd >= 1; dd >>= 1)
+                        g = max(g, __shfl_xor_sync(FULL, g, dd, L));
+                    gm = (uint32_t)(g & 0xffff) * 0x10001u;
+                    const uint32_t ch = mx ^ mx_start;
+                    const bool rel_lo = (ch & 0xffffu) != 0u && (int)(mx & 0xffffu) >= g;
+                    const bool rel_hi = (ch >> 16) != 0u && (int)(mx >> 16) >= g;
+                    if (rel_lo || rel_hi) {
+                        const T t = LT::ho_of(mx, k);
+                        int jlo = 0, jhi = 0;
+#pragma unroll
+                        for (int j = S - 1; j >= 0; --j) {
+                            const uint32_t dx = X[j] ^ t;
+                            if ((dx & 0xffffu) == 0u)
+                                jlo = j;
+                            if ((dx >> 16) == 0u)
+                                jhi = j;
+                        }
+                        if (rel_lo) {
+                            br_lo = rc;
+                            bj_lo = jlo;
+                            bv_lo = g;
+                        }
+                        if (rel_hi) {
+                            br_hi = rc;
+                            bj_hi = jhi;
+                            bv_hi = g;
+                        }
+                    }
+                }
+            }
             if constexpr (LAZY) {
                 // lazy-F (Alg. 1): shift the F leaving each virtual lane into
                 // the next one (lane L-1's low half into lane 0's high half)
@@ -233,6 +302,9 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 if (has_next && gl == L - 1 && rc < len)
                     reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, fb);
             } else {
+                // the chunk boundary's F leaves lane 0's low half decayed by S*e
+                if (has_prev && gl == 0)
+                    F = LT::addmax(bf16 | 0x80000000u, wS, F);
                 // scan of both halves at once, then the first half's outgoing
                 // F (low half of lane L-1) folded into the second half
                 T x = F;
@@ -245,7 +317,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 x = LT::addmax(fadd_u32(gb, m16, neg_lo), wfold, x);  // (-32768, low half of gb) + fold
                 T cin = __shfl_up_sync(FULL, x, 1, L);
                 if (gl == 0)
-                    cin = fadd_u32(gb, m16, (uint32_t)LT::BX);  // (0, low half of gb)
+                    cin = fadd_u32(gb, m16, bf16);  // (boundary F or 0, low half of gb)
                 c_prev = cin;
                 hlast = LT::last_corr(X[S - 1], cin, k);
                 // the next chunk reads the high halves (this chunk's last position)
@@ -253,6 +325,32 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                     reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, x);
             }
         }
+    }
+    if constexpr (ENDS) {
+        // the lane's best note (larger value, then smaller column, then the
+        // low half: its positions come first), then the group's best lane.
+        // Notes are compared by the value they were made at: a half that
+        // only tied the maximum in a later column kept an older, lower note,
+        // while the cell that set the alignment's score noted exactly it.
+        const int slo = bv_lo, shi = bv_hi;
+        const bool hi_wins = shi > slo || (shi == slo && br_hi >= 0 && (br_lo < 0 || br_hi < br_lo));
+        int bs = hi_wins ? shi : slo;
+        int br = hi_wins ? br_hi : br_lo;
+        int bq = hi_wins ? L * S + gl * S + bj_hi : gl * S + bj_lo;
+#pragma unroll
+        for (int dd = L / 2; dd >= 1; dd >>= 1) {
+            const int os = __shfl_xor_sync(FULL, bs, dd, L);
+            const int orr = __shfl_xor_sync(FULL, br, dd, L);
+            const int oq = __shfl_xor_sync(FULL, bq, dd, L);
+            if (os > bs || (os == bs && (orr < br || (orr == br && oq < bq)))) {
+                bs = os;
+                br = orr;
+                bq = oq;
+            }
+        }
+        const bool pos = bs > k.bh;  // above the h-space zero
+        *end_r = pos ? br : -1;
+        *end_q = pos ? bq : -1;
     }
 #pragma unroll
     for (int dd = L / 2; dd >= 1; dd >>= 1)
@@ -264,13 +362,15 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
 // 128 registers a thread), the most each segment length fits without spills
 // (short segments serve short queries, which are latency-bound and want the
 // extra warps)
-template <int S, bool D0>
+template <int S, bool D0, bool ENDS = false>
 struct SplitMinBlocks {
-    static constexpr int value = D0 ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2) : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
+    static constexpr int value = D0 && !ENDS ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2)
+                                 : ENDS      ? (S <= 8 ? 4 : S <= 16 || (D0 && S <= 20) ? 3 : 2)
+                                             : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
 };
 
-template <int L, int S, bool D0, bool LAZY = false>
-__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) sw_split_kernel(const BatchArgs p)
+template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false>
+__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::value) sw_split_kernel(const BatchArgs p)
 {
     constexpr int G = 32 / L;
     constexpr int SP = SegPad<S, 4>::value;
@@ -325,10 +425,32 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0>::value) s
         const int64_t start = seq[0] >= 0 ? p.off[seq[0]] : 0;
         const int len = seq[0] >= 0 ? (int)(p.off[seq[0] + 1] - start) : 0;
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
-        const uint32_t mx = split_unit<L, S, D0, LAZY>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
-                                                       has_prev, has_next, p.bnd, gl, &lazy_steps);
-        if (gl == 0)
-            write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);
+        if constexpr (ENDS) {
+            int er = -1, eq = -1;
+            const uint32_t mx = split_unit<L, S, D0, false, true>(sprof, p.db, start, len, ncols, p.A, p.o, p.e,
+                                                                  p.one, has_prev, has_next, p.bnd, gl, nullptr,
+                                                                  &er, &eq);
+            if (gl == 0 && seq[0] >= 0) {
+                // combine with the earlier chunks (smaller query positions)
+                int s = LaneQ16::score(mx, 0, k), qe = eq >= 0 ? qbase + eq + 1 : -1, re = er >= 0 ? er + 1 : -1;
+                if (has_prev) {
+                    const int ps = p.scores[seq[0]], pq = p.q_end[seq[0]], pr = p.r_end[seq[0]];
+                    if (!(s > ps || (s == ps && s > 0 && (re < pr || (re == pr && qe < pq))))) {
+                        s = ps;
+                        qe = pq;
+                        re = pr;
+                    }
+                }
+                p.scores[seq[0]] = s;
+                p.q_end[seq[0]] = s > 0 ? qe : -1;
+                p.r_end[seq[0]] = s > 0 ? re : -1;
+            }
+        } else {
+            const uint32_t mx = split_unit<L, S, D0, LAZY>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
+                                                           has_prev, has_next, p.bnd, gl, &lazy_steps);
+            if (gl == 0)
+                write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);
+        }
     }
     // j-steps of the correction loop, counted once per warp
     if (LAZY && p.lazy_steps && lane == 0 && lazy_steps)

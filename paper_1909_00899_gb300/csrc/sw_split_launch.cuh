@@ -7,10 +7,10 @@
 
 namespace swg {
 
-template <int L, int S, bool D0, bool LAZY>
+template <int L, int S, bool D0, bool LAZY, bool ENDS = false>
 int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-    auto kern = sw_split_kernel<L, S, D0, LAZY>;
+    auto kern = sw_split_kernel<L, S, D0, LAZY, ENDS>;
     constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, 4>::value * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -40,14 +40,15 @@ int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 }
 
 // the layouts (virtual lanes, two per thread) and both passes of one method
-template <bool LAZY>
+// (ENDS: scan-F with end cells)
+template <bool LAZY, bool ENDS = false>
 int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
 {
     const bool d0 = a.min_m >= -a.o;
 #define SWG_CASE(VL, SS)                                                                     \
     if (pl.L == VL && pl.S == SS)                                                            \
-        return d0 ? launch_split_inst<VL / 2, SS, true, LAZY>(a, num_sms, st)                \
-                  : launch_split_inst<VL / 2, SS, false, LAZY>(a, num_sms, st);
+        return d0 ? launch_split_inst<VL / 2, SS, true, LAZY, ENDS>(a, num_sms, st)          \
+                  : launch_split_inst<VL / 2, SS, false, LAZY, ENDS>(a, num_sms, st);
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
     SWG_CASE(32, 16)

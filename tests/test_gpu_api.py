@@ -72,6 +72,7 @@ def test_every_compiled_layout_is_exact(sw, small_db, lane):
     for m in (37, 300, 1100):
         q = synth.residues(rng, m, 20)
         want = oracle.gotoh_batch(q, db[: off[120]], off[:121], M, 11, 1)
+        want_ends = oracle.gotoh_end_batch(q, db[: off[120]], off[:121], M, 11, 1) if lane == 4 else None
         for (L, S) in ALL_PLANS[lane]:
             prof = sw.Profile(q, M, lane, lanes=L, seg_len=S)
             sw.sw_align_batch(prof, db_d, off_d, 11, 1, out)
@@ -83,6 +84,15 @@ def test_every_compiled_layout_is_exact(sw, small_db, lane):
                 torch.cuda.synchronize()
                 np.testing.assert_array_equal(out.cpu().numpy(), want,
                                               err_msg="lazy-F lane %d L=%d S=%d m=%d" % (lane, L, S, m))
+            if lane == 4:  # end cells on the split layouts
+                qe = torch.empty(120, dtype=torch.int32, device="cuda")
+                re_ = torch.empty(120, dtype=torch.int32, device="cuda")
+                sw.sw_align_batch_ends(prof, db_d, off_d, 11, 1, out, qe, re_)
+                torch.cuda.synchronize()
+                ws, wq, wr = want_ends
+                np.testing.assert_array_equal(out.cpu().numpy(), ws)
+                np.testing.assert_array_equal(re_.cpu().numpy(), wr, err_msg="ends L=%d S=%d m=%d" % (L, S, m))
+                np.testing.assert_array_equal(qe.cpu().numpy(), wq, err_msg="ends L=%d S=%d m=%d" % (L, S, m))
             prof.free()
 
 

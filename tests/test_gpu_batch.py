@@ -178,6 +178,25 @@ def test_int16_ceiling(sw, kind):
     np.testing.assert_array_equal(got, want)
 
 
+def test_int16_ceiling_end_cells(sw):
+    """Alignments whose score leaves the s16x2 range are flagged and their
+    end cells recomputed exactly with int32 lanes (split layout, AUTO)."""
+    M = np.full((20, 20), -4, np.int8)
+    np.fill_diagonal(M, 11)
+    rng = np.random.default_rng(1006)
+    q = synth.residues(rng, 3100, 20)
+    seqs = [q[:k] for k in (2975, 2979, 3000, 3100)] + [synth.residues(rng, 500, 20)]
+    seqs.append(np.concatenate([synth.residues(rng, 40, 20), q[:3050]]))
+    db, off = pack_list(seqs)
+    db_d, off_d = db_to_dev(db, off)
+    ws, wq, wr = oracle.gotoh_end_batch(q, db, off, M, 11, 1)
+    assert ws.max() > 32767
+    gs, gq, gr = _ends(sw, q, M, sw.SW_LANE_AUTO, db_d, off_d, len(seqs), 11, 1)
+    np.testing.assert_array_equal(gs, ws)
+    np.testing.assert_array_equal(gr, wr)
+    np.testing.assert_array_equal(gq, wq)
+
+
 def test_empty_inputs(sw):
     rng = np.random.default_rng(1006)
     M = synth.protein_matrix(rng)
@@ -359,7 +378,47 @@ def test_lazyf_pairs_exact_and_counts_steps(sw):
     assert related > 3 * unrelated
 
 
-@pytest.mark.parametrize("lane", ["auto", "i32"])
+def _ends(sw, q, M, kind, db_d, off_d, n, o, e):
+    prof = sw.Profile(q, M, kind)
+    sc = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    qe = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    re_ = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    sw.sw_align_batch_ends(prof, db_d, off_d, o, e, sc, qe, re_)
+    torch.cuda.synchronize()
+    prof.free()
+    return sc.cpu().numpy(), qe.cpu().numpy(), re_.cpu().numpy()
+
+
+END_LANES = ["auto", "i32", "i16x2q", "i16x2"]
+
+
+@pytest.mark.parametrize("lane", END_LANES)
+def test_end_cells_with_ties(sw, lane):
+    """Many cells reach the same maximum (DNA, +1/-1, cheap gaps, repeated
+    copies): the reported end cell is the first in column order, then the
+    smallest query position, as in the oracle; matrices on both sides of the
+    shorter corrected pass's condition; one- and multi-chunk queries."""
+    rng = np.random.default_rng(1203)
+    kind = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32, "i16x2q": sw.SW_LANE_I16X2Q,
+            "i16x2": sw.SW_LANE_I16X2}[lane]
+    for M, o, e in ((synth.dna_matrix(match=1, mismatch=-1), 2, 1), (synth.dna_matrix(match=1, mismatch=-3), 2, 1)):
+        for qlen in (30, 700, 2600):
+            q = synth.residues(rng, qlen, 4)
+            refs = [synth.residues(rng, int(n), 4) for n in rng.integers(1, 400, 40)]
+            refs += [np.concatenate([q[:50], synth.residues(rng, 30, 4), q[:50]]) for _ in range(5)]
+            refs += [np.concatenate([synth.residues(rng, 20, 4), q[qlen // 2:qlen // 2 + 60]] * 3) for _ in range(5)]
+            db, off = pack_list(refs)
+            db_d, off_d = db_to_dev(db, off)
+            n = len(off) - 1
+            ws, wq, wr = oracle.gotoh_end_batch(q, db, off, M, o, e)
+            gs, gq, gr = _ends(sw, q, M, kind, db_d, off_d, n, o, e)
+            msg = "min M %d m=%d" % (M.min(), qlen)
+            np.testing.assert_array_equal(gs, ws, err_msg=msg)
+            np.testing.assert_array_equal(gr, wr, err_msg=msg)
+            np.testing.assert_array_equal(gq, wq, err_msg=msg)
+
+
+@pytest.mark.parametrize("lane", END_LANES)
 def test_end_cells_match_oracle(sw, lane):
     """Scores and end cells of every alignment equal the oracle's (first
     cell in column order), across single- and multi-chunk queries."""
@@ -369,8 +428,9 @@ def test_end_cells_match_oracle(sw, lane):
     db, off = synth.pack(lens.astype(np.int64), rng, 20)
     db_d, off_d = db_to_dev(db, off)
     n = len(off) - 1
-    kind = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32}[lane]
-    for qlen in (1, 40, 300, 700, 1500):
+    kind = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32, "i16x2q": sw.SW_LANE_I16X2Q,
+            "i16x2": sw.SW_LANE_I16X2}[lane]
+    for qlen in (1, 40, 300, 700, 1500, 3000, 5200):
         q = synth.residues(rng, qlen, 20)
         ws, wq, wr = oracle.gotoh_end_batch(q, db, off, M, 11, 1)
         prof = sw.Profile(q, M, kind)
