@@ -113,9 +113,6 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     // run-time 65536: the half-word moves below stay IMADs on the FMA pipe
     const uint32_t m16 = one << 16;
     const int rot = (gl + L - 1) & (L - 1);  // source lane of the diagonal
-    // scan-F: the chunk boundary's F enters lane 0's low half as its carry,
-    // decaying by S*e through the segment (high half untouched)
-    const T wS = (uint32_t)((-S * e) & 0xffff);
     // ENDS, per half: the column, segment index and h-space value of the
     // half's last note (value 0: none)
     int br_lo = -1, bj_lo = 0, bv_lo = 0, br_hi = -1, bj_hi = 0, bv_hi = 0;
@@ -149,17 +146,14 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
             T hd = v;
             T F = k.xzero;
             uint32_t lo_in = xinit16;
-            uint32_t bf16 = (uint32_t)LT::BX;  // scan-F: the boundary F (16 bits), no carry by default
             if (has_prev) {
                 const uint32_t bh = __shfl_sync(FULL, my_h16, rr, L);
-                const uint32_t bf = __shfl_sync(FULL, my_f, rr, L);
                 lo_in = hb16;
                 hb16 = bh;
                 if (LAZY) {
+                    const uint32_t bf = __shfl_sync(FULL, my_f, rr, L);
                     if (gl == 0)
                         F = bf;
-                } else {
-                    bf16 = bf;
                 }
             }
             if (gl == 0)
@@ -302,9 +296,15 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 if (has_next && gl == L - 1 && rc < len)
                     reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, fb);
             } else {
-                // the chunk boundary's F leaves lane 0's low half decayed by S*e
-                if (has_prev && gl == 0)
-                    F = LT::addmax(bf16 | 0x80000000u, wS, F);
+                // scan-F: the chunk boundary's F is lane 0's low-half carry
+                // (fetched here, after the pass, so that it holds no register
+                // during it) and leaves that segment decayed by S*e
+                uint32_t bf16 = (uint32_t)LT::BX;  // no carry
+                if (has_prev) {
+                    bf16 = __shfl_sync(FULL, my_f, rr, L);
+                    if (gl == 0)
+                        F = LT::addmax(bf16 | 0x80000000u, (uint32_t)((-S * e) & 0xffff), F);
+                }
                 // scan of both halves at once, then the first half's outgoing
                 // F (low half of lane L-1) folded into the second half
                 T x = F;
