@@ -110,6 +110,15 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     const uint32_t xinit16 = (uint32_t)(LT::BX - o);
     uint32_t hb16 = xinit16;  // previous chunk's last X at the previous column (16 bits, lane 0)
     T mx = k.hzero;
+    // ENDS: the running maximum kept per half segment (ENB blocks of whole
+    // pairs, the same one vimax3 per pair), so that a row recovery scans only
+    // the block that reached the new maximum
+    constexpr int ENB = 2;
+    static_assert(!ENDS || S % 2 == 0, "end cells: even segment length");
+    T mxb[ENDS ? ENB : 1];
+#pragma unroll
+    for (int b = 0; b < (ENDS ? ENB : 1); ++b)
+        mxb[b] = k.hzero;
     // run-time 65536: the half-word moves below stay IMADs on the FMA pipe
     const uint32_t m16 = one << 16;
     const int rot = (gl + L - 1) & (L - 1);  // source lane of the diagonal
@@ -160,7 +169,6 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 hd = fadd_u32(v, m16, lo_in);  // (lo_in, low half of v)
 
             T hpair = k.hzero;
-            const T mx_start = mx;
             if (!LAZY && __any_sync(FULL, LT::carry_pos(c_prev, k))) {
                 T d = LT::d0_of(c_prev, k);
 #pragma unroll
@@ -188,12 +196,16 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                         E[j] = LT::e_next(Ej, X[j], k);
                         F = LT::addmax(F, k.negE, ho);
                     }
-                    if (j & 1)
-                        mx = LT::max3(mx, hpair, h);
-                    else if (j == S - 1)
+                    if (j & 1) {
+                        if constexpr (ENDS)
+                            mxb[(j / 2) * ENB / (S / 2)] = LT::max3(mxb[(j / 2) * ENB / (S / 2)], hpair, h);
+                        else
+                            mx = LT::max3(mx, hpair, h);
+                    } else if (j == S - 1) {
                         mx = LT::max2(mx, h);
-                    else
+                    } else {
                         hpair = h;
+                    }
                 }
             } else {
 #pragma unroll
@@ -209,49 +221,70 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                     else
                         E[j] = LT::e_next(E[j], X[j], k);
                     F = LT::addmax(F, k.negE, ho);
-                    if (j & 1)
-                        mx = LT::max3(mx, hpair, h);
-                    else if (j == S - 1)
+                    if (j & 1) {
+                        if constexpr (ENDS)
+                            mxb[(j / 2) * ENB / (S / 2)] = LT::max3(mxb[(j / 2) * ENB / (S / 2)], hpair, h);
+                        else
+                            mx = LT::max3(mx, hpair, h);
+                    } else if (j == S - 1) {
                         mx = LT::max2(mx, h);
-                    else
+                    } else {
                         hpair = h;
+                    }
                 }
             }
             if constexpr (ENDS) {
                 // Only a cell that raises the group's running maximum can be
                 // the end cell (a later cell that merely ties it comes after
                 // the one that set it), so the halves are looked at only in
-                // columns where some half rose above that maximum (gm); the
-                // group maximum is then re-reduced, and each half that rose
-                // to it notes the first cell (smallest j) whose X is h - o of
-                // the maximum.
-                const bool cand = mx != mx_start && LT::max2(mx, gm) != gm;
-                if (__any_sync(FULL, cand)) {
+                // columns where some half rose above that maximum (gm).  The
+                // group maximum g is then re-reduced; if it rose, each half
+                // with a block that reached g (in this column, g being new)
+                // notes the first cell (smallest j) of its first such block
+                // whose X is h - o of g.
+                mx = mxb[0];
+#pragma unroll
+                for (int b = 1; b < ENB; b += 2)
+                    mx = b + 1 < ENB ? LT::max3(mx, mxb[b], mxb[b + 1]) : LT::max2(mx, mxb[b]);
+                if (__any_sync(FULL, LT::max2(mx, gm) != gm)) {
                     int g = max((int)(mx & 0xffffu), (int)(mx >> 16));
 #pragma unroll
                     for (int dd = L / 2; dd >= 1; dd >>= 1)
                         g = max(g, __shfl_xor_sync(FULL, g, dd, L));
+                    const bool rose = g > (int)(gm & 0xffffu);
                     gm = (uint32_t)(g & 0xffff) * 0x10001u;
-                    const uint32_t ch = mx ^ mx_start;
-                    const bool rel_lo = (ch & 0xffffu) != 0u && (int)(mx & 0xffffu) >= g;
-                    const bool rel_hi = (ch >> 16) != 0u && (int)(mx >> 16) >= g;
-                    if (rel_lo || rel_hi) {
-                        const T t = LT::ho_of(mx, k);
+                    int blo = -1, bhi = -1;
+#pragma unroll
+                    for (int b = ENB - 1; b >= 0; --b) {
+                        if ((int)(mxb[b] & 0xffffu) >= g)
+                            blo = b;
+                        if ((int)(mxb[b] >> 16) >= g)
+                            bhi = b;
+                    }
+                    if (rose && (blo >= 0 || bhi >= 0)) {
+                        const T t = LT::ho_of(gm, k);
                         int jlo = 0, jhi = 0;
 #pragma unroll
-                        for (int j = S - 1; j >= 0; --j) {
-                            const uint32_t dx = X[j] ^ t;
-                            if ((dx & 0xffffu) == 0u)
-                                jlo = j;
-                            if ((dx >> 16) == 0u)
-                                jhi = j;
+                        for (int b = ENB - 1; b >= 0; --b) {
+                            if (b == blo || b == bhi) {
+#pragma unroll
+                                for (int j = S - 1; j >= 0; --j) {
+                                    if ((j / 2) * ENB / (S / 2) != b)
+                                        continue;
+                                    const uint32_t dx = X[j] ^ t;
+                                    if (b == blo && (dx & 0xffffu) == 0u)
+                                        jlo = j;
+                                    if (b == bhi && (dx >> 16) == 0u)
+                                        jhi = j;
+                                }
+                            }
                         }
-                        if (rel_lo) {
+                        if (blo >= 0) {
                             br_lo = rc;
                             bj_lo = jlo;
                             bv_lo = g;
                         }
-                        if (rel_hi) {
+                        if (bhi >= 0) {
                             br_hi = rc;
                             bj_hi = jhi;
                             bv_hi = g;
@@ -365,7 +398,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
 template <int S, bool D0, bool ENDS = false>
 struct SplitMinBlocks {
     static constexpr int value = D0 && !ENDS ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2)
-                                 : ENDS      ? (S <= 8 ? 4 : S <= 16 || (D0 && S <= 20) ? 3 : 2)
+                                 : ENDS      ? (D0 ? (S <= 8 ? 4 : S <= 20 ? 3 : 2) : (S <= 8 ? 3 : 2))
                                              : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
 };
 
