@@ -110,10 +110,11 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     const uint32_t xinit16 = (uint32_t)(LT::BX - o);
     uint32_t hb16 = xinit16;  // previous chunk's last X at the previous column (16 bits, lane 0)
     T mx = k.hzero;
-    // ENDS: the running maximum kept per half segment (ENB blocks of whole
-    // pairs, the same one vimax3 per pair), so that a row recovery scans only
-    // the block that reached the new maximum
-    constexpr int ENB = 2;
+    // ENDS: the running maximum kept per block of positions (ENB blocks of
+    // whole pairs, the same one vimax3 per pair), so that a row recovery
+    // scans only the block that reached the new maximum; four blocks where
+    // the two-CTA register budget has room for them, else two
+    constexpr int ENB = S >= 24 ? 4 : 2;
     static_assert(!ENDS || S % 2 == 0, "end cells: even segment length");
     T mxb[ENDS ? ENB : 1];
 #pragma unroll
