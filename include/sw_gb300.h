@@ -152,9 +152,9 @@ int sw_align_batch(const sw_profile *prof, const uint8_t *db_residues,
  * positions of the first cell, in column order (smallest reference position,
  * then smallest query position), whose H equals the score; -1, -1 when the
  * score is 0.  Runs on the profile's layout when it is split s16x2 (the
- * automatic choice; a few instructions per column over the score-only call,
- * flagged alignments rescored with int32 end cells), on its int32 layout
- * otherwise (about 1.6x the cost of the int32 score-only call).
+ * automatic choice; about 1.2x the cost of the score-only call, flagged
+ * alignments rescored with int32 end cells), on its int32 layout otherwise
+ * (about 1.6x the cost of the int32 score-only call).
  * q_end_out, r_end_out: device int32[n_db].
  */
 int sw_align_batch_ends(const sw_profile *prof, const uint8_t *db_residues,
