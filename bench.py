@@ -562,6 +562,24 @@ def run_pairs(args):
             res[name]["flagged_fraction_per_class"] = {
                 k: float((s[w["kinds"] == c] >= 127 - 1).mean()) for k, c in
                 (("copy95", 0), ("deletion", 1), ("insertion", 2), ("copy99", 3))}
+    # end cells (what mate rescue places a read by), automatic lane
+    qe_t = torch.empty(n, dtype=torch.int32, device="cuda")
+    re_t = torch.empty(n, dtype=torch.int32, device="cuda")
+    fe = lambda: sw.sw_align_pairs_ends(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, qe_t, re_t, stream=st)
+    for _ in range(args.warmup):
+        fe()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_events_ms(fe, st))
+    ends = {"gcups": cells / (np.mean(ms) * 1e-3) / 1e9, "ms": float(np.mean(ms))}
+    ids_e = np.sort(np.random.default_rng(4).choice(n, size=min(n, 2000), replace=False))
+    sbe = _pairs_subset(w, ids_e)
+    we = oracle.gotoh_end_pairs(sbe["q"], sbe["q_off"], sbe["r"], sbe["r_off"], w["M"], w["o"], w["e"])
+    got_e = (out.cpu().numpy()[ids_e], qe_t.cpu().numpy()[ids_e], re_t.cpu().numpy()[ids_e])
+    if not all(np.array_equal(a, b) for a, b in zip(got_e, we)):
+        raise SystemExit("pairs: sampled end cells differ from the oracle")
+    ends["check"] = {"sampled": int(ids_e.size), "mismatches": 0}
     steps = torch.zeros(1, dtype=torch.int64, device="cuda")
     lz = lambda: sw.sw_align_lazyf_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, lazy_steps=steps, stream=st)
     lz()
@@ -606,7 +624,7 @@ def run_pairs(args):
             "data": "synthetic", "config": {"workload": "1M DNA reads (150 bp; 30% 95%-id, 10% 40-200 bp indel, "
                                                         "60% 99%-id) vs own 2 kbp windows, +1/-4, o=6 e=1",
                                             "n_pairs": n, "cells": cells},
-            "by_lane": res, "lazyf": lazy, "scan_vs_lazyf": lazy["ms"] / best["ms"],
+            "by_lane": res, "with_end_cells": ends, "lazyf": lazy, "scan_vs_lazyf": lazy["ms"] / best["ms"],
             "per_class": per_class, "largest_margin_class": worst,
             "check": {"sampled": int(sample.size), "mismatches": 0}}
     if not args.no_cpu_baseline:
@@ -624,7 +642,7 @@ def run_pairs(args):
 
 def run_width(args):
     """Lazy-F against the vector width (the GPU analogue of Fig. 1): int32
-    lanes, fixed query lengths, lanes per alignment L = 8, 16, 32 (segment
+    lanes, fixed query lengths, lanes per alignment L = 4, 8, 16, 32 (segment
     length m / L); the lazy-F corrective factor C (correction-loop j-steps
     per main-pass j-step) and GCUPS of lazy-F and scan-F on the same layout."""
     import numpy as np
@@ -632,7 +650,7 @@ def run_width(args):
 
     from paper_1909_00899_gb300 import sw, synth
     torch.cuda.set_device(0)
-    w = synth.workload_protein_scale(n_db=args.n_db, qlens=(256, 512))
+    w = synth.workload_protein_scale(n_db=args.n_db, qlens=(128, 256, 512))
     M = w["M"]
     db_d = torch.from_numpy(w["db"]).cuda()
     off_d = torch.from_numpy(w["off"]).cuda()
@@ -642,7 +660,9 @@ def run_width(args):
     steps = torch.zeros(1, dtype=torch.int64, device="cuda")
     total = int(w["off"][-1])
     rows = []
-    for q, layouts in ((w["queries"][0], ((8, 32), (16, 16), (32, 8))), (w["queries"][1], ((16, 32), (32, 16)))):
+    for q, layouts in ((w["queries"][0], ((4, 32), (8, 16), (16, 8))),
+                       (w["queries"][1], ((8, 32), (16, 16), (32, 8))),
+                       (w["queries"][2], ((16, 32), (32, 16)))):
         cells = len(q) * total
         for L, S in layouts:
             prof = sw.Profile(q, M, sw.SW_LANE_I32, lanes=L, seg_len=S)
@@ -663,7 +683,7 @@ def run_width(args):
     line = {"metric": "lazy-F corrective factor and GCUPS vs lanes per alignment (int32)",
             "value": max(r["scan_vs_lazyf"] for r in rows), "unit": "x (scan-F over lazy-F, best width)",
             "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "protein queries m=256, 512 vs %d log-normal sequences (%d residues), o=11 e=1"
+            "config": {"workload": "protein queries m=128, 256, 512 vs %d log-normal sequences (%d residues), o=11 e=1"
                                    % (h.n, total)},
             "rows": rows}
     print(json.dumps(line), flush=True)

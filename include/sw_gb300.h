@@ -92,7 +92,7 @@ int sw_profile_build(const uint8_t *query, int32_t qlen,
  * per alignment (the paper's p, a power of two up to 32) and seg_len query
  * positions per lane (segLen); both 0 selects the built-in table.  Only the
  * shapes the kernels are compiled for are accepted (SW_ERR_INVALID
- * otherwise): int32 {4x8, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16,
+ * otherwise): int32 {4x8, 4x32, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16,
  * 8x32, 16x32, 32x32}, s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
  * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}, split s16x2 (virtual lanes)
  * {16x8, 32x8, 32x16, 64x8, 64x16, 64x20, 64x24, 64x32}.  Used by the autotuner.
@@ -221,6 +221,24 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r,
                    const int8_t *subst_matrix, int32_t alphabet,
                    int32_t gap_open, int32_t gap_extend, int32_t lane_type,
                    int32_t *scores_out, void *cuda_stream);
+
+/*
+ * sw_align_pairs_ends — sw_align_pairs plus where each pair's best local
+ * alignment ends, as sw_align_batch_ends defines it: q_end_out[k],
+ * r_end_out[k] = the 1-based query and reference positions of the first
+ * cell in column order (smallest reference position, then smallest query
+ * position) whose H equals the score; -1, -1 when the score is 0.  This is
+ * what a mate-rescue caller places a read by.  Split s16x2 kernels for
+ * SW_LANE_AUTO and SW_LANE_I16X2Q (flagged pairs rescored with int32 end
+ * cells), int32 kernels for the other lane types.  q_end_out, r_end_out:
+ * device int32[n_pairs].  Errors and synchronisation as sw_align_pairs.
+ */
+int sw_align_pairs_ends(const uint8_t *q, const int64_t *q_off, const uint8_t *r,
+                        const int64_t *r_off, int64_t n_pairs,
+                        const int8_t *subst_matrix, int32_t alphabet,
+                        int32_t gap_open, int32_t gap_extend, int32_t lane_type,
+                        int32_t *scores_out, int32_t *q_end_out,
+                        int32_t *r_end_out, void *cuda_stream);
 
 /*
  * sw_align_lazyf_pairs — as sw_align_pairs with the lazy-F correction loop

@@ -158,6 +158,18 @@ def brute_end(q, r, M, o, e):
     return s, qe.value, re_.value
 
 
+def gotoh_end_pairs(q, q_off, r, r_off, M, o, e):
+    """Scores, q_end, r_end (int32[n] each) of pair k: q[q_off[k]:q_off[k+1]]
+    against r[r_off[k]:r_off[k+1]], one oracle_gotoh_end call per pair."""
+    n = len(q_off) - 1
+    out = np.zeros(n, dtype=np.int32)
+    qe = np.zeros(n, dtype=np.int32)
+    re_ = np.zeros(n, dtype=np.int32)
+    for k in range(n):
+        out[k], qe[k], re_[k] = gotoh_end(q[q_off[k]:q_off[k + 1]], r[r_off[k]:r_off[k + 1]], M, o, e)
+    return out, qe, re_
+
+
 def gotoh_end_batch(query, db, db_off, M, o, e, nthreads=None):
     """Scores, q_end, r_end (int32[n_db] each) of one query against every
     db sequence."""

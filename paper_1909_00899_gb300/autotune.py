@@ -20,7 +20,8 @@ BINS = (64, 128, 256, 512, 1024, 2048, 4096, 1 << 30)
 CANDIDATES = {
     sw.SW_LANE_I16X2: ((8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24),
                        (32, 32)),
-    sw.SW_LANE_I32: ((4, 8), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 32)),
+    sw.SW_LANE_I32: ((4, 8), (4, 32), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32),
+                     (32, 32)),
     # split-query s16x2: virtual lanes (two per thread)
     sw.SW_LANE_I16X2Q: ((16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (64, 20), (64, 24), (64, 32)),
 }

@@ -102,8 +102,8 @@ const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
 // split-query s16x2: virtual lanes (two per thread)
 const Choice kQ16[] = {{16, 8}, {32, 8}, {64, 8}, {64, 16}, {64, 32}};
 // every (lanes, segment length) the batch kernels are instantiated for
-const Choice kAllI32[] = {{4, 8},  {8, 8},   {8, 16},  {16, 8},  {16, 16}, {32, 8},
-                          {32, 12}, {32, 16}, {8, 32},  {16, 32}, {32, 32}};
+const Choice kAllI32[] = {{4, 8},   {4, 32}, {8, 8},  {8, 16},  {16, 8}, {16, 16},
+                          {32, 8},  {32, 12}, {32, 16}, {8, 32}, {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
 const Choice kAllQ16[] = {{16, 8}, {32, 8}, {32, 16}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 32}};
@@ -114,7 +114,7 @@ bool plan_supported(int lane, int L, int S)
                       : lane == SW_LANE_I16X2 ? kAllI16
                       : lane == SW_LANE_I8X4  ? kAllI8
                                               : kAllQ16;
-    const int n = lane == SW_LANE_I32 ? 11 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 8);
+    const int n = lane == SW_LANE_I32 ? 12 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 8);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;
@@ -703,16 +703,18 @@ int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db, int32_t gap
                       db->order, db->total, lazy_steps);
 }
 
+// q_end / r_end: end cells wanted (scan-F; split s16x2 or int32 pair kernels)
 static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off, int64_t n_pairs,
                const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open, int32_t gap_extend,
                int32_t lane_type, int32_t *scores_out, void *cuda_stream, bool lazy,
-               unsigned long long *lazy_steps)
+               unsigned long long *lazy_steps, int32_t *q_end = nullptr, int32_t *r_end = nullptr)
 {
+    const bool ends = q_end != nullptr;
     if (n_pairs < 0)
         return fail(SW_ERR_INVALID, "n_pairs < 0 (%lld)", (long long)n_pairs);
     if (n_pairs > INT32_MAX - 1024)
         return fail(SW_ERR_INVALID, "n_pairs too large (%lld)", (long long)n_pairs);
-    if (n_pairs > 0 && (!q || !q_off || !r || !r_off || !scores_out))
+    if (n_pairs > 0 && (!q || !q_off || !r || !r_off || !scores_out || (ends && !r_end)))
         return fail(SW_ERR_INVALID, "null device pointer");
     if (!subst_matrix)
         return fail(SW_ERR_INVALID, "subst_matrix is NULL");
@@ -744,6 +746,8 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
     // automatic: split s16x2 (one pair per group, no byte permutes), measured
     // fastest on reads vs windows
     int lane = lazy ? SW_LANE_I32 : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2Q : lane_type);
+    if (ends && lane != SW_LANE_I16X2Q)
+        lane = SW_LANE_I32;  // end cells: split s16x2 or int32 kernels
     // query-length classes of the lane type; the packed classes must fit
     const Choice *tab = kPairI32;
     int ncls = kPairI32N;
@@ -823,6 +827,8 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
     a.scores = scores_out;
     a.one = 1;
     a.lazy_steps = lazy_steps;
+    a.q_end = q_end;
+    a.r_end = r_end;
     const int32_t thresh = flag_threshold(lane, gap_open, maxM);
     int64_t begin = 0;
     for (int k = 0; k < ncls; ++k) {
@@ -836,7 +842,8 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
                        : lane == SW_LANE_I8X4  ? swg::LK_I8X4
                                                : swg::LK_I16X2Q;
         a.flag_thresh = thresh;
-        kr = swg::launch_pairs(lk, tab[k].L, tab[k].S, lazy, a, cls, nullptr, cnt, sms, st);
+        kr = ends ? swg::launch_pairs_ends(lk, tab[k].L, tab[k].S, a, cls, nullptr, cnt, sms, st)
+                  : swg::launch_pairs(lk, tab[k].L, tab[k].S, lazy, a, cls, nullptr, cnt, sms, st);
         if (kr)
             return cuda_fail(kr, "pair kernel launch");
         if (lane != SW_LANE_I32) {
@@ -850,8 +857,10 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
                 ++j;
             a.counter = counters + 2 * k + 1;
             a.flag_thresh = INT32_MAX;
-            kr = swg::launch_pairs(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, false, a, cl, list_count + k, cnt,
-                                   sms, st);
+            kr = ends ? swg::launch_pairs_ends(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, a, cl, list_count + k,
+                                               cnt, sms, st)
+                      : swg::launch_pairs(swg::LK_I32, kPairI32[j].L, kPairI32[j].S, false, a, cl, list_count + k,
+                                          cnt, sms, st);
             if (kr)
                 return cuda_fail(kr, "rescore kernel launch");
         }
@@ -866,6 +875,17 @@ int sw_align_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, con
 {
     return pairs_impl(q, q_off, r, r_off, n_pairs, subst_matrix, alphabet, gap_open, gap_extend, lane_type,
                       scores_out, cuda_stream, false, nullptr);
+}
+
+int sw_align_pairs_ends(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
+                        int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
+                        int32_t gap_extend, int32_t lane_type, int32_t *scores_out, int32_t *q_end_out,
+                        int32_t *r_end_out, void *cuda_stream)
+{
+    if (n_pairs > 0 && (!q_end_out || !r_end_out))
+        return fail(SW_ERR_INVALID, "q_end_out / r_end_out is NULL");
+    return pairs_impl(q, q_off, r, r_off, n_pairs, subst_matrix, alphabet, gap_open, gap_extend, lane_type,
+                      scores_out, cuda_stream, false, nullptr, n_pairs > 0 ? q_end_out : nullptr, r_end_out);
 }
 
 int sw_align_lazyf_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,

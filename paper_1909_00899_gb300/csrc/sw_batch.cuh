@@ -295,11 +295,11 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
         }
         *end_r = mx > 0 ? best_r : -1;
         *end_q = mx > 0 ? bq : -1;
-        return mx;
-    }
+    } else {
 #pragma unroll
-    for (int dd = L / 2; dd >= 1; dd >>= 1)
-        mx = LT::max2(mx, __shfl_xor_sync(FULL, mx, dd, L));
+        for (int dd = L / 2; dd >= 1; dd >>= 1)
+            mx = LT::max2(mx, __shfl_xor_sync(FULL, mx, dd, L));
+    }
     return mx;
 }
 

@@ -55,6 +55,8 @@ struct PairArgs {
     int32_t flag_thresh;      // packed lanes: true score at which a cell is rescored
     unsigned long long *lazy_steps;  // optional statistics of the lazy-F loop
     int32_t min_m;            // smallest substitution score (shorter corrected pass: see sw_lanes.cuh)
+    int32_t *q_end;           // end cells (1-based query / reference position), ENDS pair kernels
+    int32_t *r_end;
 };
 
 // batch launchers (sw_k_i32.cu, sw_k_i16.cu, sw_k_i8.cu), declared in
@@ -64,6 +66,9 @@ struct PairArgs {
 // (*count_dev <= n_hint).
 int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
                  int64_t n_hint, int num_sms, cudaStream_t st);
+// the same with end cells (scan-F; lane LK_I16X2Q or LK_I32, sw_k_pairs_e.cu)
+int launch_pairs_ends(int lane, int L, int S, const PairArgs &a, const int32_t *list, const int32_t *count_dev,
+                      int64_t n_hint, int num_sms, cudaStream_t st);
 
 // Query-length classes of the pair kernel: class k holds pairs with
 // qlen <= q[k] (and > q[k-1]); class n holds longer queries.

@@ -14,6 +14,7 @@ int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
                : d0 ? launch_batch_inst<LaneI32D, LL, SS, false>(a, num_sms, st)      \
                     : launch_batch_inst<LaneI32, LL, SS, false>(a, num_sms, st);
     SWG_CASE(4, 8)
+    SWG_CASE(4, 32)
     SWG_CASE(8, 8)
     SWG_CASE(8, 16)
     SWG_CASE(16, 8)
@@ -34,6 +35,7 @@ int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaS
     if (pl.L == LL && pl.S == SS)     \
         return launch_batch_inst<LaneI32, LL, SS, false, true>(a, num_sms, st);
     SWG_CASE(4, 8)
+    SWG_CASE(4, 32)
     SWG_CASE(8, 8)
     SWG_CASE(8, 16)
     SWG_CASE(16, 8)

@@ -12,10 +12,13 @@
 
 namespace swg {
 
-template <class LT, int L, int S, bool LAZY>
+// ENDS (int32 lanes, scan-F): also the end cell of each pair's best
+// alignment into p.q_end / p.r_end (1-based, -1 when the score is 0).
+template <class LT, int L, int S, bool LAZY, bool ENDS = false>
 __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const int32_t *__restrict__ list,
                                                        const int32_t *__restrict__ count_dev, int64_t n_list)
 {
+    static_assert(!ENDS || (LT::CELLS == 1 && !LAZY), "pair end cells: int32 scan-F");
     using T = typename LT::T;
     using Elem = typename LT::Elem;
     constexpr int CELLS = LT::CELLS;
@@ -92,10 +95,22 @@ __global__ void __launch_bounds__(256) sw_pairs_kernel(const PairArgs p, const i
         }
         __syncwarp(FULL);
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
-        const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
-                                                  false, nullptr, gl, lazy_steps);
-        if (gl == 0)
-            write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), pid, false, p.flag_thresh, p.scores);
+        if constexpr (ENDS) {
+            int er = -1, eq = -1;
+            const T mx = striped_unit<LT, L, S, false, true>(pbase, p.r, start, len, ncols, A, p.o, p.e, p.one,
+                                                             false, false, nullptr, gl, lazy_steps, &er, &eq);
+            if (gl == 0 && pid[0] >= 0) {
+                const int sc = (int)mx;
+                p.scores[pid[0]] = sc;
+                p.q_end[pid[0]] = sc > 0 ? eq + 1 : -1;
+                p.r_end[pid[0]] = sc > 0 ? er + 1 : -1;
+            }
+        } else {
+            const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
+                                                      false, nullptr, gl, lazy_steps);
+            if (gl == 0)
+                write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), pid, false, p.flag_thresh, p.scores);
+        }
         __syncwarp(FULL);  // profiles are rewritten by the next unit
     }
     // j-steps of the lazy-F correction loop, counted once per warp
@@ -110,11 +125,11 @@ constexpr size_t pair_smem_per_warp(int A)
     return (size_t)32 * LT::CELLS * (A + 2) * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
 }
 
-template <class LT, int L, int S, bool LAZY>
+template <class LT, int L, int S, bool LAZY, bool ENDS = false>
 int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
                       int num_sms, cudaStream_t st)
 {
-    auto kern = sw_pairs_kernel<LT, L, S, LAZY>;
+    auto kern = sw_pairs_kernel<LT, L, S, LAZY, ENDS>;
     const size_t per_warp = pair_smem_per_warp<LT, S>(a.A);
     int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
     const size_t smem = per_warp * warps;
@@ -145,8 +160,9 @@ int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *cou
 // holds the first half of its query in the low halves and the second half
 // in the high halves (2L virtual lanes, sw_split.cuh); each group stages its
 // pair's profile as (low position, high position) pairs in its own slice of
-// shared memory, row A the unknown residue, row A+1 inert.
-template <int L, int S, bool D0>
+// shared memory, row A the unknown residue, row A+1 inert.  ENDS: also the
+// end cell of each pair's best alignment (1-based, -1 when the score is 0).
+template <int L, int S, bool D0, bool ENDS = false>
 __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, const int32_t *__restrict__ list,
                                                              const int32_t *__restrict__ count_dev, int64_t n_list)
 {
@@ -208,19 +224,32 @@ __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, c
         }
         __syncwarp(FULL);
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
-        const uint32_t mx =
-            split_unit<L, S, D0>(gprof, p.r, start, len, ncols, A, p.o, p.e, p.one, false, false, nullptr, gl);
-        if (gl == 0)
-            write_scores<LaneQ16>(mx, k, pid, false, p.flag_thresh, p.scores);
+        if constexpr (ENDS) {
+            int er = -1, eq = -1;
+            const uint32_t mx = split_unit<L, S, D0, false, true>(gprof, p.r, start, len, ncols, A, p.o, p.e,
+                                                                  p.one, false, false, nullptr, gl, nullptr, &er,
+                                                                  &eq);
+            if (gl == 0 && pid[0] >= 0) {
+                const int sc = LaneQ16::score(mx, 0, k);
+                p.scores[pid[0]] = sc;
+                p.q_end[pid[0]] = sc > 0 ? eq + 1 : -1;
+                p.r_end[pid[0]] = sc > 0 ? er + 1 : -1;
+            }
+        } else {
+            const uint32_t mx =
+                split_unit<L, S, D0>(gprof, p.r, start, len, ncols, A, p.o, p.e, p.one, false, false, nullptr, gl);
+            if (gl == 0)
+                write_scores<LaneQ16>(mx, k, pid, false, p.flag_thresh, p.scores);
+        }
         __syncwarp(FULL);  // the profile is rewritten by the next unit
     }
 }
 
-template <int L, int S, bool D0>
+template <int L, int S, bool D0, bool ENDS = false>
 int launch_pairs_split_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
                             int num_sms, cudaStream_t st)
 {
-    auto kern = sw_pairs_split_kernel<L, S, D0>;
+    auto kern = sw_pairs_split_kernel<L, S, D0, ENDS>;
     const size_t per_warp = (size_t)32 * (a.A + 2) * SegPad<S, 4>::value * 4;
     int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
     const size_t smem = per_warp * warps;

@@ -33,7 +33,7 @@ EXPORTS = (
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
-    "sw_align_batch_ends", "sw_plan_query",
+    "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends",
 )
 
 
@@ -77,6 +77,8 @@ def lib():
         L.sw_align_batch_ends.argtypes = [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
         L.sw_align_pairs.restype = ctypes.c_int
         L.sw_align_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
+        L.sw_align_pairs_ends.restype = ctypes.c_int
+        L.sw_align_pairs_ends.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp]
         L.sw_db_create.restype = ctypes.c_int
         L.sw_db_create.argtypes = [_vp, _vp, _i64, _vp, ctypes.POINTER(_vp)]
         L.sw_db_free.restype = ctypes.c_int
@@ -247,6 +249,22 @@ def sw_align_pairs(q, q_off, r, r_off, subst_matrix, gap_open, gap_extend, score
                                 int(gap_open), int(gap_extend), int(lane_type),
                                 _dev_ptr(scores_out, "int32"), _stream(stream)))
     return scores_out
+
+
+def sw_align_pairs_ends(q, q_off, r, r_off, subst_matrix, gap_open, gap_extend, scores_out, q_end_out, r_end_out,
+                        lane_type=SW_LANE_AUTO, stream=None):
+    """sw_align_pairs plus the 1-based end cell (q_end_out, r_end_out) of
+    each pair's best alignment (-1, -1 when the score is 0)."""
+    M = np.ascontiguousarray(subst_matrix, dtype=np.int8)
+    n = int(q_off.numel()) - 1
+    if int(r_off.numel()) - 1 != n:
+        raise ValueError("q_off and r_off must have the same length")
+    _check(lib().sw_align_pairs_ends(_dev_ptr(q, "uint8"), _dev_ptr(q_off, "int64"), _dev_ptr(r, "uint8"),
+                                     _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
+                                     int(gap_open), int(gap_extend), int(lane_type),
+                                     _dev_ptr(scores_out, "int32"), _dev_ptr(q_end_out, "int32"),
+                                     _dev_ptr(r_end_out, "int32"), _stream(stream)))
+    return scores_out, q_end_out, r_end_out
 
 
 class Database:

@@ -353,6 +353,45 @@ def test_pairs_unknown_residues(sw, kind):
         np.testing.assert_array_equal(got, want, err_msg="o=%d e=%d" % (o, e))
 
 
+@pytest.mark.parametrize("kind", ["auto", "i16x2q", "i32", "i16x2"])
+def test_pairs_end_cells(sw, kind):
+    """sw_align_pairs_ends: scores and end cells of every pair equal the
+    oracle's (first cell in column order), reads vs windows with planted
+    copies, ties from a +1/-1 matrix, and a +100 diagonal whose scores leave
+    the s16x2 range (flagged pairs rescored with int32 end cells)."""
+    lane = {"auto": sw.SW_LANE_AUTO, "i16x2q": sw.SW_LANE_I16X2Q, "i32": sw.SW_LANE_I32,
+            "i16x2": sw.SW_LANE_I16X2}[kind]
+    rng = np.random.default_rng(1106)
+    w = synth.workload_reads(n_pairs=300)
+    cases = [(w["q"], w["q_off"], w["r"], w["r_off"], w["M"], w["o"], w["e"])]
+    qlens = rng.integers(1, 513, 200).astype(np.int64)
+    rlens = rng.integers(1, 700, 200).astype(np.int64)
+    q, q_off = synth.pack(qlens, rng, 4)
+    r, r_off = synth.pack(rlens, rng, 4)
+    cases.append((q, q_off, r, r_off, synth.dna_matrix(match=1, mismatch=-1), 2, 1))
+    big = np.full((4, 4), -20, np.int8)
+    np.fill_diagonal(big, 100)
+    qs = [synth.residues(rng, int(n), 4) for n in (400, 500, 512)]
+    rs = [np.concatenate([synth.residues(rng, 30, 4), x, synth.residues(rng, 30, 4)]) for x in qs]
+    qb, qbo = pack_list(qs)
+    rb, rbo = pack_list(rs)
+    cases.append((qb, qbo, rb, rbo, big, 20, 2))
+    for (q, q_off, r, r_off, M, o, e) in cases:
+        n = len(q_off) - 1
+        ws, wq, wr = oracle.gotoh_end_pairs(q, q_off, r, r_off, M, o, e)
+        qd, qo = db_to_dev(q, q_off)
+        rd, ro = db_to_dev(r, r_off)
+        sc = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        qe = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        re_ = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        sw.sw_align_pairs_ends(qd, qo, rd, ro, M, o, e, sc, qe, re_, lane_type=lane)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(sc.cpu().numpy(), ws)
+        np.testing.assert_array_equal(re_.cpu().numpy(), wr)
+        np.testing.assert_array_equal(qe.cpu().numpy(), wq)
+    assert ws.max() > 32767
+
+
 def test_lazyf_pairs_exact_and_counts_steps(sw):
     """Lazy-F pairs equal the oracle; its correction loop (the corrective
     factor C of Sec. I) runs far more on related read/window pairs (long
