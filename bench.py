@@ -769,7 +769,7 @@ def run_ragged(args):
     # autotune against the database itself (one query per length bin)
     table = autotune.tune(h, M, 11, 1, lengths=[48, 100, 200, 400, 800, 1600, 3200], reps=1)
     out = torch.empty((len(queries), h.n), dtype=torch.int32, device="cuda")
-    ba = BatchAligner(h, M, 11, 1, table=table).prepare(queries, out)
+    ba = BatchAligner(h, M, 11, 1, table=table, streams=args.streams).prepare(queries, out)
     st = ba.stream
     for _ in range(args.warmup):
         ba.run()

@@ -92,10 +92,12 @@ int sw_profile_build(const uint8_t *query, int32_t qlen,
  * per alignment (the paper's p, a power of two up to 32) and seg_len query
  * positions per lane (segLen); both 0 selects the built-in table.  Only the
  * shapes the kernels are compiled for are accepted (SW_ERR_INVALID
- * otherwise): int32 {4x8, 4x32, 8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16,
- * 8x32, 16x32, 32x32}, s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
+ * otherwise): int32 {1x16, 1x32, 4x8, 4x32, 8x8, 8x16, 16x8, 16x16, 32x8,
+ * 32x12, 32x16, 8x32, 16x32, 32x32} (1 lane: one thread per alignment, no
+ * scan), s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
  * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}, split s16x2 (virtual lanes)
- * {16x8, 32x8, 32x16, 64x8, 64x16, 64x20, 64x24, 64x32}.  Used by the autotuner.
+ * {2x16, 2x32, 16x8, 32x8, 32x16, 64x8, 64x16, 64x20, 64x24, 64x32} (2
+ * virtual lanes: one thread per alignment).  Used by the autotuner.
  */
 int sw_profile_build_ex(const uint8_t *query, int32_t qlen,
                         const int8_t *subst_matrix, int32_t alphabet,

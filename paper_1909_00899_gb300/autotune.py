@@ -20,10 +20,12 @@ BINS = (64, 128, 256, 512, 1024, 2048, 4096, 1 << 30)
 CANDIDATES = {
     sw.SW_LANE_I16X2: ((8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24),
                        (32, 32)),
-    sw.SW_LANE_I32: ((4, 8), (4, 32), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32),
-                     (32, 32)),
+    # one lane (one thread per alignment, no scan) up to warp-wide groups
+    sw.SW_LANE_I32: ((1, 16), (1, 32), (4, 8), (4, 32), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12),
+                     (32, 16), (16, 32), (32, 32)),
     # split-query s16x2: virtual lanes (two per thread)
-    sw.SW_LANE_I16X2Q: ((16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (64, 20), (64, 24), (64, 32)),
+    sw.SW_LANE_I16X2Q: ((2, 16), (2, 32), (16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (64, 20), (64, 24),
+                        (64, 32)),
 }
 
 
@@ -114,6 +116,8 @@ def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I16X2Q, 
             for (L, S) in CANDIDATES[lane]:
                 if L * S > 4 * max(m, 16):
                     continue  # mostly padding
+                if (m + L * S - 1) // (L * S) > 8:
+                    continue  # many chunks: each re-streams the database
                 ms = _time_layout(db, q, M, o, e, lane, L, S, out, reps, stream)
                 g = m * cells_db / (ms * 1e-3) / 1e9
                 cands.append((g, lane, L, S))

@@ -102,11 +102,11 @@ const Choice kI8[] = {{8, 16}, {16, 16}, {32, 16}};
 // split-query s16x2: virtual lanes (two per thread)
 const Choice kQ16[] = {{16, 8}, {32, 8}, {64, 8}, {64, 16}, {64, 32}};
 // every (lanes, segment length) the batch kernels are instantiated for
-const Choice kAllI32[] = {{4, 8},   {4, 32}, {8, 8},  {8, 16},  {16, 8}, {16, 16},
-                          {32, 8},  {32, 12}, {32, 16}, {8, 32}, {16, 32}, {32, 32}};
+const Choice kAllI32[] = {{1, 16}, {1, 32}, {4, 8},   {4, 32},  {8, 8},  {8, 16}, {16, 8},
+                          {16, 16}, {32, 8}, {32, 12}, {32, 16}, {8, 32}, {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
-const Choice kAllQ16[] = {{16, 8}, {32, 8}, {32, 16}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 32}};
+const Choice kAllQ16[] = {{2, 16}, {2, 32}, {16, 8}, {32, 8}, {32, 16}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 32}};
 
 bool plan_supported(int lane, int L, int S)
 {
@@ -114,7 +114,7 @@ bool plan_supported(int lane, int L, int S)
                       : lane == SW_LANE_I16X2 ? kAllI16
                       : lane == SW_LANE_I8X4  ? kAllI8
                                               : kAllQ16;
-    const int n = lane == SW_LANE_I32 ? 12 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 8);
+    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 10);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;

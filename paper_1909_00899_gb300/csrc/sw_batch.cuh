@@ -72,11 +72,11 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
     using T = typename LT::T;
     constexpr int CELLS = LT::CELLS;
     constexpr int SP = SegPad<S, LT::VEC>::value;
-    constexpr int LOGL = L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : L == 16 ? 4 : 5;
+    constexpr int LOGL = L == 1 ? 0 : L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : L == 16 ? 4 : 5;
     constexpr unsigned FULL = 0xffffffffu;
 
     const typename LT::K k = LT::consts(o, e, S, one);
-    T negW[LOGL];  // scan hop weights -(2^i)*S*e
+    T negW[LOGL > 0 ? LOGL : 1];  // scan hop weights -(2^i)*S*e (none for one lane)
 #pragma unroll
     for (int i = 0; i < LOGL; ++i)
         negW[i] = LT::splat(-(1 << i) * S * e);
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
     constexpr int G = 32 / L;
     constexpr int QC = L * S;
     constexpr unsigned FULL = 0xffffffffu;
-    static_assert(L >= 2 && L <= 32 && (L & (L - 1)) == 0, "lanes per alignment: power of two");
+    static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "lanes per alignment: power of two");
     static_assert(!LAZY || LT::VEC != 16, "lazy-F kernel: int32 or s16x2 lanes");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -13,6 +13,8 @@ int launch_batch_i32(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms,
         return lazy ? launch_batch_inst<LaneI32, LL, SS, true>(a, num_sms, st)        \
                : d0 ? launch_batch_inst<LaneI32D, LL, SS, false>(a, num_sms, st)      \
                     : launch_batch_inst<LaneI32, LL, SS, false>(a, num_sms, st);
+    SWG_CASE(1, 16)
+    SWG_CASE(1, 32)
     SWG_CASE(4, 8)
     SWG_CASE(4, 32)
     SWG_CASE(8, 8)
@@ -34,6 +36,8 @@ int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaS
 #define SWG_CASE(LL, SS)              \
     if (pl.L == LL && pl.S == SS)     \
         return launch_batch_inst<LaneI32, LL, SS, false, true>(a, num_sms, st);
+    SWG_CASE(1, 16)
+    SWG_CASE(1, 32)
     SWG_CASE(4, 8)
     SWG_CASE(4, 32)
     SWG_CASE(8, 8)

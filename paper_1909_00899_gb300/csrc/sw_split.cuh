@@ -84,12 +84,12 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
     using LT = LaneQ16;
     using T = uint32_t;
     constexpr int SP = SegPad<S, 4>::value;
-    constexpr int LOGL = L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : L == 16 ? 4 : 5;
+    constexpr int LOGL = L == 1 ? 0 : L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : L == 16 ? 4 : 5;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int V = 4;
 
     const LT::K k = LT::consts_pb(o, e, S, one, split_pb<D0>(o));
-    T negW[LOGL];
+    T negW[LOGL > 0 ? LOGL : 1];  // scan hop weights (none for one thread)
 #pragma unroll
     for (int i = 0; i < LOGL; ++i)
         negW[i] = LT::splat(-(1 << i) * S * e);

@@ -49,6 +49,8 @@ int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStrea
     if (pl.L == VL && pl.S == SS)                                                            \
         return d0 ? launch_split_inst<VL / 2, SS, true, LAZY, ENDS>(a, num_sms, st)          \
                   : launch_split_inst<VL / 2, SS, false, LAZY, ENDS>(a, num_sms, st);
+    SWG_CASE(2, 16)
+    SWG_CASE(2, 32)
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
     SWG_CASE(32, 16)

@@ -15,11 +15,11 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 ALL_PLANS = {
-    1: [(4, 8), (4, 32), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (8, 32), (16, 32),
-        (32, 32)],
+    1: [(1, 16), (1, 32), (4, 8), (4, 32), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16),
+        (8, 32), (16, 32), (32, 32)],
     2: [(8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24), (32, 32)],
     3: [(8, 16), (16, 16), (32, 16)],
-    4: [(16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (64, 20), (64, 24), (64, 32)],
+    4: [(2, 16), (2, 32), (16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (64, 20), (64, 24), (64, 32)],
 }
 
 
