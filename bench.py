@@ -594,8 +594,19 @@ def run_pairs(args):
     steps.zero_()
     flush.zero_()
     lms = _events_ms(lz, st)
-    lazy = {"gcups": cells / (lms * 1e-3) / 1e9, "ms": lms,
+    lazy = {"gcups": cells / (lms * 1e-3) / 1e9, "ms": lms, "lane": "int32",
             "C_factor": float(steps.item()) * 32 / cells}
+    # lazy-F on the split s16x2 layout too (the layout scan-F runs on); the
+    # comparison takes the faster lazy-F
+    lzq = lambda: sw.sw_align_lazyf_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, stream=st,
+                                          lane_type=sw.SW_LANE_I16X2Q)
+    lzq()
+    flush.zero_()
+    lqms = _events_ms(lzq, st)
+    lazy_split = {"gcups": cells / (lqms * 1e-3) / 1e9, "ms": lqms, "lane": "s16x2_split"}
+    lazy_int32 = lazy
+    if lqms < lms:
+        lazy = dict(lazy_split, C_factor_int32=lazy_int32["C_factor"])
     # scan-F vs lazy-F and the lazy-F corrective factor C per read class
     per_class = {}
     for cname, c in (("copy95", 0), ("deletion", 1), ("insertion", 2), ("copy99", 3)):
@@ -613,9 +624,15 @@ def run_pairs(args):
         lf()
         c_fac = float(steps.item()) * 32 / scells
         lfm = _events_ms(lf, st, 2)
+        lq = lambda: sw.sw_align_lazyf_pairs(sq, sqo, sr, sro, w["M"], w["o"], w["e"], so, stream=st,
+                                             lane_type=sw.SW_LANE_I16X2Q)
+        lq()
+        lqm = _events_ms(lq, st, 2)
         per_class[cname] = {"pairs": int(len(ids)), "scan_gcups": scells / (sms * 1e-3) / 1e9,
-                            "lazyf_gcups": scells / (lfm * 1e-3) / 1e9, "scan_vs_lazyf": lfm / sms,
-                            "lazyf_C_factor": c_fac}
+                            "lazyf_gcups": scells / (min(lfm, lqm) * 1e-3) / 1e9,
+                            "lazyf_gcups_by_lane": {"int32": scells / (lfm * 1e-3) / 1e9,
+                                                    "s16x2_split": scells / (lqm * 1e-3) / 1e9},
+                            "scan_vs_lazyf": min(lfm, lqm) / sms, "lazyf_C_factor_int32": c_fac}
     worst = max(per_class, key=lambda k: per_class[k]["scan_vs_lazyf"])
     # exactness on a sample, every lane type agreed already in the tests
     sw.sw_align_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, stream=st)
@@ -632,7 +649,9 @@ def run_pairs(args):
             "data": "synthetic", "config": {"workload": "1M DNA reads (150 bp; 30% 95%-id, 10% 40-200 bp indel, "
                                                         "60% 99%-id) vs own 2 kbp windows, +1/-4, o=6 e=1",
                                             "n_pairs": n, "cells": cells},
-            "by_lane": res, "with_end_cells": ends, "lazyf": lazy, "scan_vs_lazyf": lazy["ms"] / best["ms"],
+            "by_lane": res, "with_end_cells": ends, "lazyf": lazy,
+            "lazyf_by_lane": {"int32": lazy_int32, "s16x2_split": lazy_split},
+            "scan_vs_lazyf": lazy["ms"] / best["ms"],
             "per_class": per_class, "largest_margin_class": worst,
             "check": {"sampled": int(sample.size), "mismatches": 0}}
     if not args.no_cpu_baseline:

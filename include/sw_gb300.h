@@ -257,6 +257,20 @@ int sw_align_lazyf_pairs(const uint8_t *q, const int64_t *q_off,
                          int32_t gap_extend, int32_t *scores_out,
                          unsigned long long *lazy_steps, void *cuda_stream);
 
+/* sw_align_lazyf_pairs on a chosen layout: SW_LANE_I16X2Q runs the
+ * correction loop on the split s16x2 pair kernel (the layout of the
+ * automatic sw_align_pairs; flagged pairs are rescored with the scan-F
+ * int32 kernel), any other lane type on int32 lanes.  lazy_steps as above,
+ * counted per warp (a split warp step covers twice the cells of an int32
+ * one). */
+int sw_align_lazyf_pairs_lane(const uint8_t *q, const int64_t *q_off,
+                              const uint8_t *r, const int64_t *r_off,
+                              int64_t n_pairs, const int8_t *subst_matrix,
+                              int32_t alphabet, int32_t gap_open,
+                              int32_t gap_extend, int32_t lane_type,
+                              int32_t *scores_out,
+                              unsigned long long *lazy_steps, void *cuda_stream);
+
 /* sw_align_lazyf_db with the same optional lazy-F step counter. */
 int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
                             int32_t gap_open, int32_t gap_extend,

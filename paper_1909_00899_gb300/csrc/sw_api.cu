@@ -745,7 +745,9 @@ static int pairs_impl(const uint8_t *q, const int64_t *q_off, const uint8_t *r, 
     shape.maxM = maxM;
     // automatic: split s16x2 (one pair per group, no byte permutes), measured
     // fastest on reads vs windows
-    int lane = lazy ? SW_LANE_I32 : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2Q : lane_type);
+    // lazy-F: int32 lanes, or the split s16x2 layout when asked for
+    int lane = lazy ? (lane_type == SW_LANE_I16X2Q ? SW_LANE_I16X2Q : SW_LANE_I32)
+                    : (lane_type == SW_LANE_AUTO ? SW_LANE_I16X2Q : lane_type);
     if (ends && lane != SW_LANE_I16X2Q)
         lane = SW_LANE_I32;  // end cells: split s16x2 or int32 kernels
     // query-length classes of the lane type; the packed classes must fit
@@ -894,6 +896,15 @@ int sw_align_lazyf_pairs(const uint8_t *q, const int64_t *q_off, const uint8_t *
                          void *cuda_stream)
 {
     return pairs_impl(q, q_off, r, r_off, n_pairs, subst_matrix, alphabet, gap_open, gap_extend, SW_LANE_I32,
+                      scores_out, cuda_stream, true, lazy_steps);
+}
+
+int sw_align_lazyf_pairs_lane(const uint8_t *q, const int64_t *q_off, const uint8_t *r, const int64_t *r_off,
+                              int64_t n_pairs, const int8_t *subst_matrix, int32_t alphabet, int32_t gap_open,
+                              int32_t gap_extend, int32_t lane_type, int32_t *scores_out,
+                              unsigned long long *lazy_steps, void *cuda_stream)
+{
+    return pairs_impl(q, q_off, r, r_off, n_pairs, subst_matrix, alphabet, gap_open, gap_extend, lane_type,
                       scores_out, cuda_stream, true, lazy_steps);
 }
 

@@ -40,10 +40,14 @@ int launch_pairs(int lane, int L, int S, bool lazy, const PairArgs &a, const int
         SWG_CASE16(32, 16)
     } else if (lane == LK_I16X2Q) {
         // virtual lanes (two per thread), as the batch split layouts
-#define SWG_CASEQ(VL, SS)                                                                                        \
-    if (L == VL && S == SS)                                                                                      \
-        return d0_16 ? launch_pairs_split_inst<VL / 2, SS, true>(a, list, count_dev, n_hint, num_sms, st)       \
-                     : launch_pairs_split_inst<VL / 2, SS, false>(a, list, count_dev, n_hint, num_sms, st);
+#define SWG_CASEQ(VL, SS)                                                                                          \
+    if (L == VL && S == SS)                                                                                        \
+        return lazy    ? (d0_16 ? launch_pairs_split_inst<VL / 2, SS, true, false, true>(a, list, count_dev, n_hint, \
+                                                                                        num_sms, st)               \
+                                : launch_pairs_split_inst<VL / 2, SS, false, false, true>(a, list, count_dev,      \
+                                                                                         n_hint, num_sms, st))     \
+               : d0_16 ? launch_pairs_split_inst<VL / 2, SS, true>(a, list, count_dev, n_hint, num_sms, st)        \
+                       : launch_pairs_split_inst<VL / 2, SS, false>(a, list, count_dev, n_hint, num_sms, st);
         SWG_CASEQ(16, 8)
         SWG_CASEQ(16, 10)
         SWG_CASEQ(32, 8)

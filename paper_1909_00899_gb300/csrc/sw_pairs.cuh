@@ -162,10 +162,13 @@ int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *cou
 // pair's profile as (low position, high position) pairs in its own slice of
 // shared memory, row A the unknown residue, row A+1 inert.  ENDS: also the
 // end cell of each pair's best alignment (1-based, -1 when the score is 0).
-template <int L, int S, bool D0, bool ENDS = false>
+// LAZY: the lazy-F loop instead of the scan (the comparison on the same layout).
+template <int L, int S, bool D0, bool ENDS = false, bool LAZY = false>
 __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, const int32_t *__restrict__ list,
                                                              const int32_t *__restrict__ count_dev, int64_t n_list)
 {
+    static_assert(!(ENDS && LAZY), "end cells: scan-F only");
+    unsigned long long lazy_steps = 0;
     constexpr int SP = SegPad<S, 4>::value;
     constexpr int QH = L * S;  // positions per half
     constexpr int G = 32 / L;
@@ -236,20 +239,23 @@ __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, c
                 p.r_end[pid[0]] = sc > 0 ? er + 1 : -1;
             }
         } else {
-            const uint32_t mx =
-                split_unit<L, S, D0>(gprof, p.r, start, len, ncols, A, p.o, p.e, p.one, false, false, nullptr, gl);
+            const uint32_t mx = split_unit<L, S, D0, LAZY>(gprof, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
+                                                           false, nullptr, gl, &lazy_steps);
             if (gl == 0)
                 write_scores<LaneQ16>(mx, k, pid, false, p.flag_thresh, p.scores);
         }
         __syncwarp(FULL);  // the profile is rewritten by the next unit
     }
+    // j-steps of the lazy-F correction loop, counted once per warp
+    if (LAZY && p.lazy_steps && lane == 0 && lazy_steps)
+        atomicAdd(p.lazy_steps, lazy_steps);
 }
 
-template <int L, int S, bool D0, bool ENDS = false>
+template <int L, int S, bool D0, bool ENDS = false, bool LAZY = false>
 int launch_pairs_split_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
                             int num_sms, cudaStream_t st)
 {
-    auto kern = sw_pairs_split_kernel<L, S, D0, ENDS>;
+    auto kern = sw_pairs_split_kernel<L, S, D0, ENDS, LAZY>;
     const size_t per_warp = (size_t)32 * (a.A + 2) * SegPad<S, 4>::value * 4;
     int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
     const size_t smem = per_warp * warps;

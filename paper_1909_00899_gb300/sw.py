@@ -33,7 +33,7 @@ EXPORTS = (
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
-    "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends",
+    "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends", "sw_align_lazyf_pairs_lane",
 )
 
 
@@ -89,6 +89,9 @@ def lib():
             f.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
         L.sw_align_lazyf_pairs.restype = ctypes.c_int
         L.sw_align_lazyf_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp]
+        L.sw_align_lazyf_pairs_lane.restype = ctypes.c_int
+        L.sw_align_lazyf_pairs_lane.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _vp,
+                                                _vp]
         L.sw_align_lazyf_db_stats.restype = ctypes.c_int
         L.sw_align_lazyf_db_stats.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp, _vp]
         L.sw_stream_sync.restype = ctypes.c_int
@@ -322,18 +325,26 @@ def sw_align_lazyf_db(profile, db, gap_open, gap_extend, scores_out, stream=None
 
 
 def sw_align_lazyf_pairs(q, q_off, r, r_off, subst_matrix, gap_open, gap_extend, scores_out,
-                         lazy_steps=None, stream=None):
+                         lazy_steps=None, stream=None, lane_type=None):
     """Lazy-F (Alg. 1) pair scores; lazy_steps: optional int64 CUDA tensor
-    of one element that accumulates the correction loop's j-steps."""
+    of one element that accumulates the correction loop's j-steps.
+    lane_type: None (int32 lanes, sw_align_lazyf_pairs) or a lane type
+    (sw_align_lazyf_pairs_lane: SW_LANE_I16X2Q runs on the split layout)."""
     M = np.ascontiguousarray(subst_matrix, dtype=np.int8)
     n = int(q_off.numel()) - 1
     if int(r_off.numel()) - 1 != n:
         raise ValueError("q_off and r_off must have the same length")
     steps = _dev_ptr(lazy_steps, "int64") if lazy_steps is not None else None
-    _check(lib().sw_align_lazyf_pairs(_dev_ptr(q, "uint8"), _dev_ptr(q_off, "int64"), _dev_ptr(r, "uint8"),
-                                      _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
-                                      int(gap_open), int(gap_extend), _dev_ptr(scores_out, "int32"),
-                                      steps, _stream(stream)))
+    if lane_type is None:
+        _check(lib().sw_align_lazyf_pairs(_dev_ptr(q, "uint8"), _dev_ptr(q_off, "int64"), _dev_ptr(r, "uint8"),
+                                          _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
+                                          int(gap_open), int(gap_extend), _dev_ptr(scores_out, "int32"),
+                                          steps, _stream(stream)))
+    else:
+        _check(lib().sw_align_lazyf_pairs_lane(_dev_ptr(q, "uint8"), _dev_ptr(q_off, "int64"), _dev_ptr(r, "uint8"),
+                                               _dev_ptr(r_off, "int64"), n, M.ctypes.data, int(M.shape[0]),
+                                               int(gap_open), int(gap_extend), int(lane_type),
+                                               _dev_ptr(scores_out, "int32"), steps, _stream(stream)))
     return scores_out
 
 

@@ -392,6 +392,29 @@ def test_pairs_end_cells(sw, kind):
     assert ws.max() > 32767
 
 
+def test_lazyf_pairs_on_the_split_layout(sw):
+    """Lazy-F on the split s16x2 pair kernel equals the oracle (reads vs
+    windows, the gap adversary, both corrected-pass conditions) and counts
+    its correction steps."""
+    rng = np.random.default_rng(1107)
+    w = synth.workload_reads(n_pairs=400)
+    queries, refs = gap_adversary(rng, 4, 100, xlo=20, xhi=120, ylo=40, yhi=200)
+    qa, qao = pack_list([x[:512] for x in queries])
+    ra, rao = pack_list(refs)
+    for (q, q_off, r, r_off, M, o, e) in ((w["q"], w["q_off"], w["r"], w["r_off"], w["M"], w["o"], w["e"]),
+                                          (qa, qao, ra, rao, synth.dna_matrix(), 6, 1),
+                                          (qa, qao, ra, rao, synth.dna_matrix(match=2, mismatch=-5), 3, 1)):
+        want = oracle.gotoh_pairs(q, q_off, r, r_off, M, o, e)
+        qd, qo = db_to_dev(q, q_off)
+        rd, ro = db_to_dev(r, r_off)
+        out = torch.full((len(q_off) - 1,), -7, dtype=torch.int32, device="cuda")
+        steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sw.sw_align_lazyf_pairs(qd, qo, rd, ro, M, o, e, out, lazy_steps=steps, lane_type=sw.SW_LANE_I16X2Q)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        assert steps.item() > 0
+
+
 def test_lazyf_pairs_exact_and_counts_steps(sw):
     """Lazy-F pairs equal the oracle; its correction loop (the corrective
     factor C of Sec. I) runs far more on related read/window pairs (long
