@@ -480,6 +480,29 @@ def test_end_cells_with_ties(sw, lane):
             np.testing.assert_array_equal(gq, wq, err_msg=msg)
 
 
+@pytest.mark.parametrize("lane", ["auto", "i32"])
+def test_end_cells_with_unknown_residues(sw, lane):
+    """End cells when database codes >= A (unknown residues, scored as the
+    smallest matrix entry) sit inside and around the best alignments."""
+    rng = np.random.default_rng(1204)
+    kind = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32}[lane]
+    M = synth.dna_matrix(match=2, mismatch=-3)
+    for qlen in (40, 900, 2600):
+        q = synth.residues(rng, qlen, 4)
+        refs = [np.concatenate([synth.residues(rng, int(rng.integers(0, 100)), 4), q[: min(qlen, 300)],
+                                synth.residues(rng, 50, 4)]) for _ in range(30)]
+        refs += [synth.residues(rng, int(n), 4) for n in rng.integers(1, 500, 30)]
+        db, off = pack_list(refs)
+        hit = rng.random(len(db)) < 0.05
+        db[hit] = rng.choice(np.array([4, 7, 255], np.uint8), int(hit.sum()))
+        db_d, off_d = db_to_dev(db, off)
+        ws, wq, wr = oracle.gotoh_end_batch(q, db, off, M, 5, 1)
+        gs, gq, gr = _ends(sw, q, M, kind, db_d, off_d, len(refs), 5, 1)
+        np.testing.assert_array_equal(gs, ws)
+        np.testing.assert_array_equal(gr, wr)
+        np.testing.assert_array_equal(gq, wq)
+
+
 @pytest.mark.parametrize("lane", END_LANES)
 def test_end_cells_match_oracle(sw, lane):
     """Scores and end cells of every alignment equal the oracle's (first
