@@ -380,8 +380,11 @@ def main():
     # scores copied out, inside the timed region
     e2e = None if args.quick else run_e2e(w, lane, args, stream, cells_step)
 
-    # roofline of the dominant kernel (the scan-F batch kernel): cells of
-    # each query's call over that call's event-timed duration, all queries
+    # roofline of the dominant kernel: the longest query's call is its
+    # chunk launches (plus a profile build, the length order, the overflow
+    # flag and the int32 rescore, together below 0.2 % of the launch time),
+    # so its m*n over the call's event-timed duration is the kernel's cell
+    # rate; the rate over every query's call is reported beside it
     plans = []
     launches_per_step = 0
     for m in QLENS:
@@ -396,13 +399,22 @@ def main():
         # profile build (+ its int32 twin), 3 order kernels, one launch per
         # chunk, then for packed lanes the flag kernel and the int32 rescore
         launches_per_step += (2 if packed else 1) + 3 + pl["chunks"] + ((1 + pl32["chunks"]) if packed else 0)
-    plan = plans[-1]
+    i_dom = QLENS.index(max(QLENS))
+    plan = plans[i_dom]
     cells_per_op = {1: 1, 2: 2, 3: 4, 4: 2}[plan["lane_type"]]
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     # integer ALU pipe: 16 lanes/clk per SM sub-partition, 4 per SM
     peak_alu = sms * 64 * mhz * 1e6 / (6.0 / cells_per_op) / 1e9
-    kernel_gcups = sum(QLENS) * total_res / (sum(per_q) * 1e-3) / 1e9
+    all_gcups = sum(QLENS) * total_res / (sum(per_q) * 1e-3) / 1e9
+    kernel_gcups = QLENS[i_dom] * total_res / (per_q[i_dom] * 1e-3) / 1e9
+    d0 = int(M.min()) >= -o
+    if plan["lane_type"] == sw.SW_LANE_I16X2Q:
+        kname = "sw_split_kernel<%d, %d, %s, false, false>" % (plan["lanes"] // 2, plan["seg_len"],
+                                                               "true" if d0 else "false")
+    else:
+        kname = "sw_batch_kernel<lane %d, %d, %d, false, false>" % (plan["lane_type"], plan["lanes"],
+                                                                    plan["seg_len"])
     probe = None if args.quick else sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
 
     line = {
@@ -423,12 +435,17 @@ def main():
         "scan_vs_lazyf_per_query": ({str(m): (m * total_res / (t * 1e-3) / 1e9) / lazy["per_query_gcups"][str(m)]
                                      for m, t in zip(QLENS, per_q)} if lazy else None),
         "roofline": {"bound": "alu", "achieved": kernel_gcups, "peak": peak_alu, "unit": "GCUPS",
-                     "frac": kernel_gcups / peak_alu,
+                     "frac": kernel_gcups / peak_alu, "kernel": kname,
+                     "launches_per_call": plan["chunks"], "ms_per_launch": per_q[i_dom] / max(1, plan["chunks"]),
+                     "cells_per_launch": QLENS[i_dom] * total_res / max(1, plan["chunks"]),
                      "traffic": NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC else None,
                      "traffic_basis": NCU_TRAFFIC,
                      "peak_basis": ("%d SMs x 64 int lane-ops/clk (half-rate ALU pipe, 4 x 16 lanes) x %.0f MHz "
                                     "(median sampled) / %g DPX instr per cell" % (sms, mhz, 6.0 / cells_per_op)),
-                     "achieved_basis": "sum of m*n over each query's sw_align_batch call / its CUDA-event time",
+                     "achieved_basis": ("m*n of the m=%d call (its %d launches of the kernel; profile, order, "
+                                        "flag and rescore launches < 0.2 %%) / its CUDA-event time on the "
+                                        "launching stream" % (QLENS[i_dom], plan["chunks"])),
+                     "achieved_all_queries": all_gcups, "frac_all_queries": all_gcups / peak_alu,
                      "probe_gcups": probe, "frac_of_probe": (kernel_gcups / probe) if probe else None},
         "clocks": clocks,
         "e2e": e2e,
