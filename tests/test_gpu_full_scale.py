@@ -102,3 +102,76 @@ def test_reads_vs_windows_full_size_sampled(sw):
     sw.sw_align_lazyf_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], lz)
     np.testing.assert_array_equal(lz.cpu().numpy(), got)
     assert got.max() > 127  # the packed lanes overflowed somewhere and were rescored
+
+
+def _sampled_check(got, q, db, off, M, o, e, ids, err):
+    sub_db, sub_off = _subset(db, off, ids)
+    want = oracle.gotoh_batch(q, sub_db, sub_off, M, o, e)
+    np.testing.assert_array_equal(got[ids], want, err_msg=err)
+
+
+def test_ragged_batch_full_size_sampled(sw):
+    """The ragged batch at its full database size (200k log-normal
+    sequences, 80 M residues) in the benchmark's launch configuration:
+    length-stratified queries from the 10,000 (32..4096), an autotuned
+    layout per length bin, every alignment in one graph replayed over four
+    streams.  Sampled outputs against the oracle (the longest sequences
+    included), every output against the direct database call and within
+    0 <= score <= max(M) * min(m, n)."""
+    from paper_1909_00899_gb300 import autotune
+    from paper_1909_00899_gb300.batch import BatchAligner
+    rng = synth.rng_for(3)
+    M = synth.protein_matrix(rng)
+    qlens_all = synth.lengths_loguniform(rng, 10_000, 32, 4096)
+    db, off = synth.random_db(rng, 200_000, 20, "lognormal", median=300, sigma=0.76, lo=20, hi=35000)
+    order = np.argsort(qlens_all, kind="stable")
+    pick = order[np.linspace(0, len(order) - 1, 10).astype(int)]
+    queries = [synth.residues(np.random.default_rng([5, int(i)]), int(qlens_all[i]), 20) for i in pick]
+    db_d, off_d = torch.from_numpy(db).cuda(), torch.from_numpy(off).cuda()
+    h = sw.Database(db_d, off_d)
+    table = autotune.tune(h, M, 11, 1, lengths=[48, 400, 3200], reps=1)
+    out = torch.full((len(queries), h.n), -7, dtype=torch.int32, device="cuda")
+    ba = BatchAligner(h, M, 11, 1, table=table, streams=4).prepare(queries, out)
+    ba.run()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    lens = np.diff(off)
+    ids = np.unique(np.concatenate([np.random.default_rng(79).choice(h.n, 80, replace=False),
+                                    np.argsort(lens)[-4:]]))
+    direct = torch.empty(h.n, dtype=torch.int32, device="cuda")
+    for i, q in enumerate(queries):
+        _sampled_check(got[i], q, db, off, M, 11, 1, ids, "query %d (m=%d)" % (i, len(q)))
+        p = sw.Profile(q, M)
+        sw.sw_align_db(p, h, 11, 1, direct)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got[i], direct.cpu().numpy(), err_msg="graph vs direct, m=%d" % len(q))
+        p.free()
+        assert got[i].min() >= 0 and np.all(got[i] <= int(M.max()) * np.minimum(len(q), lens))
+    ba.free()
+
+
+def test_serving_full_size_sampled(sw):
+    """Serving against the full resident database (1M log-normal sequences,
+    about 350 M residues) in the benchmark's configuration (four slots, a
+    48 GB budget, Poisson arrivals): every request's scores the same alone
+    and in the mix, and sampled against the oracle."""
+    from paper_1909_00899_gb300 import serve
+    rng = synth.rng_for(4)
+    M = synth.protein_matrix(rng)
+    db, off = synth.random_db(rng, 1_000_000, 20, "lognormal", median=300, sigma=0.555, lo=20, hi=35000)
+    assert 3.0e8 < off[-1] < 4.0e8
+    db_d, off_d = torch.from_numpy(db).cuda(), torch.from_numpy(off).cuda()
+    h = sw.Database(db_d, off_d)
+    r = np.random.default_rng([6, 99])
+    qlens = synth.lengths_loguniform(r, 6, 50, 10_000)
+    queries = [synth.residues(r, int(m), 20) for m in qlens]
+    alone = serve.Server(h, M, 11, 1, slots=1, mem_budget=48 << 30).run(queries)
+    srv = serve.Server(h, M, 11, 1, slots=4, mem_budget=48 << 30)
+    mixed = srv.run(queries, serve.poisson_arrivals(np.random.default_rng(9), len(queries), 20.0))
+    lens = np.diff(off)
+    ids = np.unique(np.concatenate([np.random.default_rng(80).choice(h.n, 60, replace=False),
+                                    np.argsort(lens)[-3:]]))
+    for k, (a, b) in enumerate(zip(alone, mixed)):
+        np.testing.assert_array_equal(a.scores, b.scores, err_msg="request %d alone vs mixed" % k)
+        _sampled_check(b.scores, queries[k], db, off, M, 11, 1, ids, "request %d (m=%d)" % (k, len(queries[k])))
+    assert srv.in_use == 0
