@@ -279,18 +279,19 @@ def main():
     def lazy_lane(lazy):
         return {"s16x2": sw.SW_LANE_I16X2, "s16x2_split": sw.SW_LANE_I16X2Q}.get(lazy, sw.SW_LANE_I32)
 
-    def step(lazy=False):
+    def step(lazy=False, scan_lane=None):
         """One pass of the path: every query's profile and its alignment
         against the whole db; the independent queries are spread over the
         side streams and joined back into the current stream.  lazy: False
-        (scan-F), "int32" or "s16x2" (lazy-F on that lane type)."""
+        (scan-F), "int32", "s16x2" or "s16x2_split" (lazy-F on that lane
+        type); scan_lane: the scan-F lane type instead of --lane."""
         fork = torch.cuda.Event()
         fork.record(stream)
         profs = []
         for i, q in enumerate(w["queries"]):
             st = side[i % len(side)]
             st.wait_event(fork)
-            p = sw.Profile(q, M, lazy_lane(lazy) if lazy else lane, stream=st)
+            p = sw.Profile(q, M, lazy_lane(lazy) if lazy else (lane if scan_lane is None else scan_lane), stream=st)
             fn = sw.sw_align_lazyf_batch if lazy else sw.sw_align_batch
             fn(p, db_d, off_d, o, e, outs[i], stream=st)
             profs.append(p)
@@ -302,9 +303,9 @@ def main():
 
     step_ms = []  # this rank's per-step times of the last timed() call
 
-    def timed(nsteps, lazy=False):
+    def timed(nsteps, lazy=False, scan_lane=None):
         for _ in range(args.warmup):
-            step(lazy)
+            step(lazy, scan_lane)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -315,7 +316,7 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            profs = step(lazy)
+            profs = step(lazy, scan_lane)
             b.record(stream)
             keep.append((profs, a, b))
         torch.cuda.synchronize()
@@ -327,12 +328,12 @@ def main():
             total_ms = dist.max_over_ranks(total_ms, device="cuda")
         return total_ms
 
-    def per_query(lazy=False):
+    def per_query(lazy=False, scan_lane=None):
         """Each query's alignment call alone on the current stream, timed
         with CUDA events on that stream (the dominant kernel's launches)."""
         ms = []
         for q, out in zip(w["queries"], outs):
-            p = sw.Profile(q, M, lazy_lane(lazy) if lazy else lane, stream=stream)
+            p = sw.Profile(q, M, lazy_lane(lazy) if lazy else (lane if scan_lane is None else scan_lane), stream=stream)
             torch.cuda.synchronize()
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
@@ -359,6 +360,7 @@ def main():
     per_q = per_query()
 
     lazy = None
+    scan_i32 = None
     if not args.no_lazyf:
         lsteps = max(1, min(args.steps, 2))
         by_lane = {}
@@ -375,6 +377,13 @@ def main():
         lazy["per_query_gcups"] = {str(m): max(by_lane[k]["per_query_gcups"][str(m)] for k in by_lane)
                                    for m in QLENS}
         lazy["by_lane"] = by_lane
+        # scan-F on int32 lanes too: the plain method, method against method
+        # on the same lane type
+        ims = timed(lsteps, scan_lane=sw.SW_LANE_I32)
+        iper = per_query(scan_lane=sw.SW_LANE_I32)
+        scan_i32 = {"value": cells_step * lsteps / (ims * 1e-3) / 1e9, "unit": "GCUPS",
+                    "per_query_gcups": {str(m): m * total_res / (t * 1e-3) / 1e9 for m, t in zip(QLENS, iper)}}
+        scan_i32["vs_lazyf_int32"] = scan_i32["value"] / by_lane["int32"]["value"]
 
     # end to end through the public API: host (pinned) inputs copied in,
     # scores copied out, inside the timed region
@@ -432,6 +441,7 @@ def main():
         "streams": args.streams,
         "lazyf": lazy,
         "scan_vs_lazyf": (gcups / world / lazy["value"]) if lazy else None,
+        "scan_int32": scan_i32,
         "scan_vs_lazyf_per_query": ({str(m): (m * total_res / (t * 1e-3) / 1e9) / lazy["per_query_gcups"][str(m)]
                                      for m, t in zip(QLENS, per_q)} if lazy else None),
         "roofline": {"bound": "alu", "achieved": kernel_gcups, "peak": peak_alu, "unit": "GCUPS",
