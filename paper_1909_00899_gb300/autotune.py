@@ -1,6 +1,15 @@
 """Autotuner for the striped kernels: for each query-length bin it times
 every compiled layout (lane type x lanes per alignment x segment length) of
-sw_align_db on a sample of the database and keeps the fastest.
+sw_align_db against the database and keeps every layout's measured rate per
+processed cell.  A query then gets the layout that maximises
+
+    rate x m / (C x L x S) / (1 + 1.5 % x (C - 1)),   C = ceil(m / (L x S)),
+
+for its own length m: the rate measured in its bin, the fraction of the
+C chunks' L x S positions that are real, and a small cost per extra chunk
+launch (each re-streams the database and hands boundary rows on).  So two
+queries of the same bin can take different layouts when one of them fills a
+layout's chunks and the other would mostly pad them.
 
 The layouts are the paper's p (lanes per alignment) and segLen (positions per
 lane); the lane type decides how many alignments one register carries.  The
@@ -29,6 +38,26 @@ CANDIDATES = {
 }
 
 
+CHUNK_COST = 0.015  # per extra chunk launch, as in the library's automatic plan
+
+
+def chunks_of(m, L, S):
+    return max(1, (int(m) + L * S - 1) // (L * S))
+
+
+def admissible(m, L, S):
+    """The layouts worth timing or choosing for a query of length m: not
+    mostly padding, and at most 8 chunk launches."""
+    return L * S <= 4 * max(int(m), 16) and chunks_of(m, L, S) <= 8
+
+
+def expected_gcups(m, L, S, rate):
+    """Cells of the query per second on a layout whose measured rate per
+    processed cell is `rate`."""
+    C = chunks_of(m, L, S)
+    return rate * max(int(m), 1) / (C * L * S) / (1.0 + CHUNK_COST * (C - 1))
+
+
 def bin_of(m):
     for b in BINS:
         if m <= b:
@@ -41,23 +70,34 @@ def default_cache_path():
 
 
 class Table:
-    """Best layout per query-length bin: {bin: (lane, lanes, seg_len, gcups)}."""
+    """Measured layouts per query-length bin:
+    {bin: [(lane, lanes, seg_len, GCUPS per processed cell), ...]}."""
 
     def __init__(self, entries=None, device=""):
-        self.entries = dict(entries or {})
+        self.entries = {int(k): [tuple(c) for c in v] for k, v in (entries or {}).items()}
         self.device = device
 
     def plan(self, m):
-        """(lane_type, lanes, seg_len) for a query of length m, or None."""
-        e = self.entries.get(bin_of(m))
-        return None if e is None else tuple(e[:3])
+        """(lane_type, lanes, seg_len) for a query of length m: the bin's
+        layout with the highest expected rate at this length, or None."""
+        cands = self.entries.get(bin_of(m))
+        if not cands:
+            return None
+        ok = [c for c in cands if admissible(m, c[1], c[2])] or cands
+        best = max(ok, key=lambda c: expected_gcups(m, c[1], c[2], c[3]))
+        return tuple(best[:3])
 
     def to_json(self):
-        return {"device": self.device, "entries": {str(k): list(v) for k, v in self.entries.items()}}
+        return {"device": self.device, "version": 2,
+                "entries": {str(k): [list(c) for c in v] for k, v in self.entries.items()}}
 
     @classmethod
     def from_json(cls, d):
-        return cls({int(k): tuple(v) for k, v in d["entries"].items()}, d.get("device", ""))
+        if d.get("version", 1) < 2:
+            # one (lane, lanes, seg_len, gcups) per bin: keep it as the
+            # bin's only layout
+            return cls({int(k): [tuple(v)] for k, v in d["entries"].items()}, d.get("device", ""))
+        return cls({int(k): [tuple(c) for c in v] for k, v in d["entries"].items()}, d.get("device", ""))
 
     def save(self, path=None):
         path = path or default_cache_path()
@@ -99,8 +139,9 @@ def _time_layout(db, query, M, o, e, lane, L, S, out, reps, stream):
 
 def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I16X2Q, sw.SW_LANE_I32), reps=2, seed=0,
          device_name=None, verbose=False):
-    """Times every candidate layout for one query per length bin against the
-    resident database `db` and returns the best per bin."""
+    """Times every admissible layout for one query per length bin against
+    the resident database `db` and returns each layout's rate per processed
+    cell, per bin."""
     import torch
     rng = np.random.default_rng(seed)
     A = M.shape[0]
@@ -114,16 +155,17 @@ def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I16X2Q, 
         cands = []
         for lane in lanes:
             for (L, S) in CANDIDATES[lane]:
-                if L * S > 4 * max(m, 16):
-                    continue  # mostly padding
-                if (m + L * S - 1) // (L * S) > 8:
-                    continue  # many chunks: each re-streams the database
+                if not admissible(m, L, S):
+                    continue
                 ms = _time_layout(db, q, M, o, e, lane, L, S, out, reps, stream)
-                g = m * cells_db / (ms * 1e-3) / 1e9
-                cands.append((g, lane, L, S))
+                C = chunks_of(m, L, S)
+                # per processed cell, with the extra chunk launches of this
+                # length taken out again (expected_gcups charges them per m)
+                rate = C * L * S * cells_db / (ms * 1e-3) / 1e9 * (1.0 + CHUNK_COST * (C - 1))
+                cands.append((lane, L, S, rate))
                 if verbose:
-                    print("m=%d lane=%d L=%d S=%d: %.1f GCUPS" % (m, lane, L, S, g))
-        g, lane, L, S = max(cands)
-        best[bin_of(m)] = (lane, L, S, g)
+                    print("m=%d lane=%d L=%d S=%d: %.1f GCUPS (%.1f per processed cell)"
+                          % (m, lane, L, S, m * cells_db / (ms * 1e-3) / 1e9, rate))
+        best[bin_of(m)] = cands
     name = device_name or torch.cuda.get_device_name()
     return Table(best, name)

@@ -87,3 +87,24 @@ def test_plan_query_covers_the_query_host_only(swlib):
         swlib.sw_plan_query(-1)
     with pytest.raises(swlib.SwError):
         swlib.sw_plan_query(10, 9)
+
+
+def test_autotune_table_plans_each_query_length():
+    """The tuned table keeps every layout's rate per processed cell and picks
+    per exact length: a layout whose chunks the query fills beats a faster
+    one it would mostly pad (host logic only)."""
+    from paper_1909_00899_gb300 import autotune as at
+    Q = 4  # split s16x2 lane type
+    t = at.Table({4096: [(Q, 64, 20, 5000.0), (Q, 64, 32, 5000.0), (Q, 64, 24, 4800.0)]}, "dev")
+    assert t.plan(2100) == (Q, 64, 20)   # 2 chunks of 1280: 82 % real positions
+    assert t.plan(3000) == (Q, 64, 24)   # 2 chunks of 1536: 98 %
+    assert t.plan(4000) == (Q, 64, 32)   # 2 chunks of 2048: 98 %
+    assert t.plan(50) is None            # untuned bin: the library's own plan
+    # expected rate: measured rate x real fraction / chunk cost
+    assert abs(at.expected_gcups(4000, 64, 32, 5000.0) - 5000.0 * 4000 / 4096 / 1.015) < 1e-9
+    assert at.chunks_of(5000, 64, 20) == 4 and not at.admissible(100, 64, 32)
+    rt = at.Table.from_json(t.to_json())
+    assert all(rt.plan(m) == t.plan(m) for m in (2100, 3000, 4000))
+    # tables saved before the per-layout format: one layout per bin
+    old = at.Table.from_json({"device": "dev", "entries": {"4096": [Q, 64, 20, 4147.8]}})
+    assert old.plan(3000) == (Q, 64, 20)
