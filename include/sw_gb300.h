@@ -325,6 +325,18 @@ const char *sw_last_error(void);
 int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_second,
                        void *cuda_stream);
 
+/*
+ * sw_probe_cell_rate_pass — as sw_probe_cell_rate, for one pass of the
+ * scan-F column loop: corrected = 0 is the plain pass above; corrected = 1
+ * is the shorter corrected pass the kernels run in columns that receive a
+ * carry when every substitution score is >= -gap_open (the deferred
+ * correction of Alg. 6: the diagonal and E raised by the carry, decaying by
+ * gap_extend per position).  SW_LANE_I8X4 has no corrected pass
+ * (SW_ERR_INVALID), as has any other value of corrected.
+ */
+int sw_probe_cell_rate_pass(int32_t lane_type, int32_t corrected, int32_t iters,
+                            double *cells_per_second, void *cuda_stream);
+
 /* Library version, e.g. "0.1.0". */
 const char *sw_version(void);
 

@@ -928,10 +928,20 @@ int sw_stream_sync(void *cuda_stream, int64_t timeout_ms)
 
 int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_second, void *cuda_stream)
 {
+    return sw_probe_cell_rate_pass(lane_type, 0, iters, cells_per_second, cuda_stream);
+}
+
+int sw_probe_cell_rate_pass(int32_t lane_type, int32_t corrected, int32_t iters, double *cells_per_second,
+                            void *cuda_stream)
+{
     if (!cells_per_second)
         return fail(SW_ERR_INVALID, "cells_per_second is NULL");
     if (lane_type < SW_LANE_I32 || lane_type > SW_LANE_I16X2Q)
         return fail(SW_ERR_INVALID, "lane_type must be I32, I16X2, I8X4 or I16X2Q");
+    if (corrected != 0 && corrected != 1)
+        return fail(SW_ERR_INVALID, "corrected must be 0 or 1");
+    if (corrected && lane_type == SW_LANE_I8X4)
+        return fail(SW_ERR_INVALID, "the s8x4 lanes have no shorter corrected pass");
     if (lane_type == SW_LANE_I16X2Q)
         lane_type = SW_LANE_I16X2;  // the same cell sequence on the same lane type
     if (iters < 1)
@@ -942,7 +952,7 @@ int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_secon
     double cells = 0;
     float ms = 0;
     const int op = lane_type - 1;
-    int kr = swg::run_int_peak(op, sms * 8, 256, iters, &cells, &ms, (cudaStream_t)cuda_stream);
+    int kr = swg::run_int_peak(op, corrected != 0, sms * 8, 256, iters, &cells, &ms, (cudaStream_t)cuda_stream);
     if (kr)
         return cuda_fail(kr, "cell-rate probe");
     *cells_per_second = ms > 0 ? cells / (ms * 1e-3) : 0.0;

@@ -202,11 +202,13 @@ int launch_pair_classes(const int64_t *q_off, int64_t n_pairs, const ClassTable 
 
 // ---------------------------------------------------------------------------
 // Cell-rate probe.  Each thread updates K positions per column with the
-// exact instruction sequence of the plain scan-F pass (no loads, shuffles,
-// scan or correction), so the measured rate is the ceiling of that sequence
-// on this GPU.  op 0: int32 cells, 1: s16x2, 2: s8x4.
+// exact instruction sequence of a scan-F pass (no loads, shuffles or scan),
+// so the measured rate is the ceiling of that sequence on this GPU.  CORR:
+// the shorter corrected pass (every substitution score >= -o), which raises
+// the diagonal and E by the decaying carry d; else the plain general pass.
+// op 0: int32 cells, 1: s16x2, 2: s8x4 (plain only).
 // ---------------------------------------------------------------------------
-template <class LT>
+template <class LT, bool CORR = false>
 __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uint32_t one, int *sink)
 {
     using T = typename LT::T;
@@ -224,13 +226,21 @@ __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uin
         T hd = X[K - 1];
         T F = k.xzero;
         T hpair = k.hzero;
+        T d = LT::d0_of(X[K / 2], k);  // a carry that changes every column
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const T h = LT::h_of(hd, (j & 1) ? P1 : P0, E[j], k);
-            hd = X[j];
             const T ho = LT::ho_of(h, k);
-            X[j] = LT::addmax(F, k.negO, ho);
-            E[j] = LT::e_next(E[j], X[j], k);
+            if constexpr (CORR) {
+                hd = LT::xd_corr(X[j], d, k);
+                d = LT::dstep(d, k);
+                X[j] = LT::addmax(F, k.negO, ho);
+                E[j] = LT::e_next_corr(E[j], d, X[j], k);
+            } else {
+                hd = X[j];
+                X[j] = LT::addmax(F, k.negO, ho);
+                E[j] = LT::e_next(E[j], X[j], k);
+            }
             F = LT::addmax(F, k.negE, ho);
             if (j & 1)
                 mx = LT::max3(mx, hpair, h);
@@ -250,7 +260,8 @@ __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uin
         sink[0] = acc;
 }
 
-int run_int_peak(int op, int blocks, int threads, int iters, double *cells, float *ms, cudaStream_t st)
+int run_int_peak(int op, bool corrected, int blocks, int threads, int iters, double *cells, float *ms,
+                 cudaStream_t st)
 {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -261,8 +272,12 @@ int run_int_peak(int op, int blocks, int threads, int iters, double *cells, floa
         return (int)err;
     const uint32_t one = 1;
     auto go = [&](void) {
-        if (op == 0)
+        if (op == 0 && corrected)
+            cell_peak_kernel<LaneI32D, true><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
+        else if (op == 0)
             cell_peak_kernel<LaneI32><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
+        else if (op == 1 && corrected)
+            cell_peak_kernel<LaneI16x2D, true><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
         else if (op == 1)
             cell_peak_kernel<LaneI16x2><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
         else

@@ -126,6 +126,7 @@ int api_launch_plan(const Plan &pl, bool lazy, const BatchArgs &a, int sms, cuda
 
 // Cell-rate probe of the plain pass for the roofline: 'op' selects the
 // lane type (0 int32, 1 s16x2, 2 s8x4); returns cells updated and ms.
-int run_int_peak(int op, int blocks, int threads, int iters, double *cells, float *ms, cudaStream_t st);
+int run_int_peak(int op, bool corrected, int blocks, int threads, int iters, double *cells, float *ms,
+                 cudaStream_t st);
 
 }  // namespace swg

@@ -31,7 +31,7 @@ SW_LANE_I16X2Q = 4
 EXPORTS = (
     "sw_profile_build", "sw_profile_build_ex", "sw_profile_free", "sw_profile_free_async", "sw_profile_plan", "sw_align_batch",
     "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
-    "sw_probe_cell_rate", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
+    "sw_probe_cell_rate", "sw_probe_cell_rate_pass", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
     "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends", "sw_align_lazyf_pairs_lane",
 )
@@ -102,6 +102,8 @@ def lib():
         L.sw_version.argtypes = []
         L.sw_probe_cell_rate.restype = ctypes.c_int
         L.sw_probe_cell_rate.argtypes = [_i32, _i32, ctypes.POINTER(ctypes.c_double), _vp]
+        L.sw_probe_cell_rate_pass.restype = ctypes.c_int
+        L.sw_probe_cell_rate_pass.argtypes = [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_double), _vp]
         _lib = L
     return _lib
 
@@ -379,4 +381,11 @@ def sw_version():
 def sw_probe_cell_rate(lane_type=SW_LANE_I32, iters=4096, stream=None):
     out = ctypes.c_double(0.0)
     _check(lib().sw_probe_cell_rate(int(lane_type), int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def sw_probe_cell_rate_pass(lane_type=SW_LANE_I32, corrected=0, iters=4096, stream=None):
+    out = ctypes.c_double(0.0)
+    _check(lib().sw_probe_cell_rate_pass(int(lane_type), int(corrected), int(iters), ctypes.byref(out),
+                                         _stream(stream)))
     return out.value

@@ -62,6 +62,10 @@ def test_invalid_arguments_rejected_without_cuda(swlib):
     assert L.sw_align_batch(None, None, None, 0, 11, 1, None, None) == swlib.SW_ERR_INVALID
     assert L.sw_align_lazyf_batch(None, None, None, 0, 11, 1, None, None) == swlib.SW_ERR_INVALID
     assert L.sw_probe_cell_rate(7, 10, None, None) == swlib.SW_ERR_INVALID
+    cps = ctypes.c_double(0.0)
+    assert L.sw_probe_cell_rate_pass(1, 2, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID
+    assert L.sw_probe_cell_rate_pass(3, 1, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID
+    assert "s8x4" in swlib.sw_last_error()
 
 
 def test_plan_query_covers_the_query_host_only(swlib):

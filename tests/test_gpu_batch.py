@@ -244,6 +244,11 @@ def test_cell_rate_probe_runs(sw):
     for lane in (sw.SW_LANE_I32, sw.SW_LANE_I16X2, sw.SW_LANE_I8X4):
         r = sw.sw_probe_cell_rate(lane, 256)
         assert r > 1e9
+    # the corrected pass does more per cell than the plain one
+    for lane in (sw.SW_LANE_I32, sw.SW_LANE_I16X2):
+        plain = sw.sw_probe_cell_rate_pass(lane, 0, 1024)
+        corr = sw.sw_probe_cell_rate_pass(lane, 1, 1024)
+        assert 1e9 < corr < plain
 
 
 # ---------------------------------------------------------------------------
