@@ -68,6 +68,29 @@ def test_query_lengths_span_plans_and_chunks(sw, kind):
         np.testing.assert_array_equal(got, want, err_msg="qlen=%d" % qlen)
 
 
+@pytest.mark.parametrize("kind", ["auto", "i32", "i16x2", "lazyf16q"])
+def test_long_queries_many_chunks(sw, kind):
+    """Queries of 12,000 and 20,000 residues (10 to 33 chunk launches,
+    depending on the lane type) against a ragged database that also holds a
+    3000-residue slice of each query: high scores carried across every chunk
+    boundary, near the packed lanes' ceiling (flagged and rescored there)."""
+    rng = np.random.default_rng(1010)
+    M = synth.protein_matrix(rng)
+    for qlen in (12_000, 20_000):
+        q = synth.residues(rng, qlen, 20)
+        lens = np.concatenate([[0, 1], rng.integers(1, 800, 40)]).astype(np.int64)
+        seqs = [synth.residues(rng, int(x), 20) for x in lens]
+        start = int(rng.integers(0, qlen - 3000))
+        seqs.append(np.concatenate([synth.residues(rng, 50, 20), q[start:start + 3000],
+                                    synth.residues(rng, 50, 20)]))
+        db, off = pack_list(seqs)
+        db_d, off_d = db_to_dev(db, off)
+        want = oracle.gotoh_batch(q, db, off, M, 11, 1)
+        assert want[-1] > 15_000  # the planted slice
+        got = run(sw, kind, q, M, db_d, off_d, 11, 1)
+        np.testing.assert_array_equal(got, want, err_msg="qlen=%d" % qlen)
+
+
 @pytest.mark.parametrize("kind", LANES)
 def test_gap_adversary_dna(sw, kind):
     """Long query-side insertions (vertical gaps through many segments) with
