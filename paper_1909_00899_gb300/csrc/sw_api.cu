@@ -275,6 +275,12 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
     return swg::launch_batch_i8(pl, a, sms, st);
 }
 
+// Splitting of long sequences: pieces of at least this many columns (a
+// short query keeps a few thousand columns of serial work per item), and no
+// splitting when the overlap alone would make pieces longer than the cap.
+constexpr int64_t kMinPieceLen = 2048;
+constexpr int64_t kMaxPieceLen = 1 << 20;
+
 // pre_order / pre_total: a database handle's persistent length order and
 // residue count (then no order kernels run and nothing is read back).
 // q_end / r_end: end cells wanted (ENDS kernels: split s16x2 lanes for split
@@ -333,15 +339,36 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
             return fail(SW_ERR_INVALID, "db_offsets[n_db] < 0");
     }
 
+    // Long sequences against a short single-chunk query: split into pieces
+    // that overlap by the widest span a positive-scoring local alignment can
+    // have (m aligned pairs at most, and each column of horizontal gap costs
+    // at least e, so it spans at most m + (m * max M - 1) / e columns).  Every
+    // optimal alignment then lies inside one piece, so the best piece score is
+    // the sequence's score, while the longest work item shrinks to the piece
+    // length: a single short query no longer waits on one warp that walks the
+    // longest sequence alone.  Scores only (end cells and the lazy-F
+    // statistics keep whole sequences).
+    int32_t piece_len = 0, piece_stride = 0;
+    if (!ends && !lazy_steps && main.C == 1 && (!packed || C32 == 1) && e >= 1 && prof->maxM >= 1) {
+        const int64_t span = (int64_t)prof->qlen + ((int64_t)prof->qlen * prof->maxM - 1) / e;
+        const int64_t plen = std::max<int64_t>(2 * span, kMinPieceLen);
+        if (plen <= kMaxPieceLen) {
+            piece_len = (int32_t)plen;
+            piece_stride = (int32_t)(plen - span + 1);
+        }
+    }
+    const bool pieces = piece_len > 0;
+
     const size_t n = (size_t)n_db;
-    const int ncount = main.C + (packed ? C32 : 0) + 2;
+    const int ncount = main.C + (packed ? C32 : 0) + 3;
     const size_t sz_order = pre_order ? 0 : align_up(n * 4);
     const size_t sz_zero = align_up((2 * swg::NBINS + ncount) * 4);
     const size_t sz_list = packed ? align_up(n * 4) : 0;
     const size_t sz_bnd = chunked ? align_up((size_t)total * sizeof(int2) + 16) : 0;
+    const size_t sz_pieces = pieces ? align_up(n * sizeof(swg::Piece)) + align_up(n) : 0;
     Scratch sc;
     sc.st = st;
-    cudaError_t err = cudaMallocAsync(&sc.base, sz_order + sz_zero + sz_list + sz_bnd, st);
+    cudaError_t err = cudaMallocAsync(&sc.base, sz_order + sz_zero + sz_list + sz_bnd + sz_pieces, st);
     if (err != cudaSuccess) {
         sc.base = nullptr;
         return cuda_fail(err, "cudaMallocAsync(scratch)");
@@ -352,8 +379,11 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     int32_t *bins = zero;
     uint32_t *counters = (uint32_t *)(zero + 2 * swg::NBINS);
     int32_t *list_count = (int32_t *)(counters + main.C + (packed ? C32 : 0));
+    int32_t *n_pieces = list_count + 1;
     int32_t *list = (int32_t *)(p + sz_order + sz_zero);
     int2 *bnd = chunked ? (int2 *)(p + sz_order + sz_zero + sz_list) : nullptr;
+    swg::Piece *piece_arr = pieces ? (swg::Piece *)(p + sz_order + sz_zero + sz_list + sz_bnd) : nullptr;
+    uint8_t *split = pieces ? (uint8_t *)piece_arr + align_up(n * sizeof(swg::Piece)) : nullptr;
 
     err = cudaMemsetAsync(zero, 0, sz_zero, st);
     if (err != cudaSuccess)
@@ -385,6 +415,15 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     a.min_m = prof->minM;
     a.prof = main_prof;
     a.nchunks = main.C;
+    if (pieces) {
+        kr = swg::launch_piece_plan(off, n_db, piece_len, piece_stride, (int32_t)std::min<int64_t>(n_db, INT32_MAX),
+                                    piece_arr, n_pieces, split, scores, st, sms);
+        if (kr)
+            return cuda_fail(kr, "piece plan kernel");
+        a.pieces = piece_arr;
+        a.n_pieces = n_pieces;
+        a.split = split;
+    }
     for (int c = 0; c < main.C; ++c) {
         a.chunk = c;
         a.counter = counters + c;
@@ -401,6 +440,9 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
         a.prof = prof->d_prof32;
         a.flag_thresh = INT32_MAX;
         a.nchunks = C32;
+        a.pieces = nullptr;  // flagged sequences are rescored whole
+        a.n_pieces = nullptr;
+        a.split = nullptr;
         a.order = list;
         a.n_work = n_db;
         a.n_work_dev = list_count;

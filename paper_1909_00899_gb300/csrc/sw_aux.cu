@@ -126,6 +126,61 @@ int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32
     return (int)cudaGetLastError();
 }
 
+// Pieces of the long sequences.  The reservation of a sequence's k slots
+// retries a bounded number of times under contention; a sequence that does
+// not get its slots (the cap is reached) is aligned whole.
+__global__ void piece_plan_kernel(const int64_t *__restrict__ off, int64_t n, int32_t piece_len, int32_t stride,
+                                  int32_t cap, Piece *pieces, int32_t *n_pieces, uint8_t *split, int32_t *scores)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t start = off[i];
+        const int64_t len = off[i + 1] - start;
+        uint8_t s = 0;
+        if (len > piece_len) {
+            const int64_t k = 1 + (len - piece_len + stride - 1) / stride;
+            int32_t base = -1;
+            if (k <= cap) {
+                int32_t old = *((volatile int32_t *)n_pieces);
+                for (int tries = 0; tries < (1 << 16) && old + k <= cap; ++tries) {
+                    const int32_t prev = atomicCAS(n_pieces, old, old + (int32_t)k);
+                    if (prev == old) {
+                        base = old;
+                        break;
+                    }
+                    old = prev;
+                }
+            }
+            if (base >= 0) {
+                for (int64_t j = 0; j < k; ++j) {
+                    const int64_t c0 = j * stride;
+                    Piece pc;
+                    pc.start = start + c0;
+                    pc.seq = (int32_t)i;
+                    pc.len = (int32_t)(len - c0 < piece_len ? len - c0 : piece_len);
+                    pieces[base + j] = pc;
+                }
+                scores[i] = 0;
+                s = 1;
+            }
+        }
+        split[i] = s;
+    }
+}
+
+int launch_piece_plan(const int64_t *off, int64_t n, int32_t piece_len, int32_t stride, int32_t cap,
+                      Piece *pieces, int32_t *n_pieces, uint8_t *split, int32_t *scores, cudaStream_t st,
+                      int num_sms)
+{
+    if (n <= 0)
+        return (int)cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms * 8)
+        blocks = (int64_t)num_sms * 8;
+    piece_plan_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n, piece_len, stride, cap, pieces, n_pieces, split,
+                                                         scores);
+    return (int)cudaGetLastError();
+}
+
 __global__ void flag_overflow_list_kernel(const int32_t *__restrict__ scores, const int32_t *__restrict__ list,
                                           int64_t n, int32_t thresh, int32_t *out, int32_t *out_count)
 {

@@ -15,6 +15,16 @@ struct Plan {
 };
 
 // Parameters of one launch of the batch kernel (one query chunk).
+// One piece of a long database sequence (a window of its columns), aligned
+// as if it were a sequence of its own; the pieces of one sequence overlap by
+// at least the number of columns a positive-scoring local alignment of the
+// query can span, so the largest piece score is the sequence's score.
+struct Piece {
+    int64_t start;  // first residue (index into the concatenated database)
+    int32_t seq;    // the sequence it belongs to
+    int32_t len;    // columns
+};
+
 struct BatchArgs {
     const int8_t *prof;       // raw striped profile of this plan: [C][A][L][S] int8 (M values)
     int32_t A;                // alphabet size; profile row A is the inert "no residue" row
@@ -36,6 +46,13 @@ struct BatchArgs {
     int32_t *r_end;
     int32_t min_m;            // smallest substitution score of the profile (the split
                               // kernels' shorter corrected pass needs min_m >= -o)
+    // long sequences split into overlapping pieces (single-chunk scores
+    // only; null otherwise): work items [0, *n_pieces) are pieces, whose
+    // scores are combined by atomicMax, then the entries of order, skipping
+    // the sequences whose split flag is set
+    const Piece *pieces;
+    const int32_t *n_pieces;
+    const uint8_t *split;
 };
 
 // Parameters of the pair kernel (each pair has its own query).
@@ -94,6 +111,14 @@ int launch_length_order(const int64_t *off, int64_t n, int32_t *order, int32_t *
 // Sequences whose score reached thresh -> list (count in *count, zero at launch).
 int launch_flag_overflow(const int32_t *scores, int64_t n, int32_t thresh, int32_t *list, int32_t *count,
                          cudaStream_t st, int num_sms);
+// Long sequences (more than piece_len residues) -> overlapping pieces of
+// piece_len columns every stride columns, at most cap pieces in all (a
+// sequence that no longer fits stays whole); split[i] tells which, and a
+// split sequence's score is zeroed for the pieces' atomicMax.
+// *n_pieces zero at launch.
+int launch_piece_plan(const int64_t *off, int64_t n, int32_t piece_len, int32_t stride, int32_t cap,
+                      Piece *pieces, int32_t *n_pieces, uint8_t *split, int32_t *scores, cudaStream_t st,
+                      int num_sms);
 
 }  // namespace swg
 

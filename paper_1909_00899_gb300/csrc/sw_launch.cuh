@@ -28,8 +28,10 @@ int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
         per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (!a.n_work_dev) {
-        // no more blocks than there are work units for their warps
-        const int64_t units = (a.n_work + LT::CELLS - 1) / LT::CELLS;
+        // no more blocks than there are work units for their warps (pieces
+        // of long sequences: at most n_work more items)
+        const int64_t items = a.pieces ? 2 * a.n_work : a.n_work;
+        const int64_t units = (items + LT::CELLS - 1) / LT::CELLS;
         const int64_t per_block = (BATCH_THREADS / 32) * (32 / L);
         const int64_t need = (units + per_block - 1) / per_block;
         if (need < grid)

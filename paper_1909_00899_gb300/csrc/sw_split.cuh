@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int grp = lane / L;
-    const int64_t n_work = p.n_work_dev ? (int64_t)(*p.n_work_dev) : p.n_work;
+    const int n_pieces = p.n_pieces ? *p.n_pieces : 0;
+    const int64_t n_work = (p.n_work_dev ? (int64_t)(*p.n_work_dev) : p.n_work) + n_pieces;
     const bool has_prev = p.chunk > 0;
     const bool has_next = p.chunk + 1 < p.nchunks;
     const LaneQ16::K k = LaneQ16::consts_pb(p.o, p.e, S, p.one, split_pb<D0>(p.o));
@@ -453,11 +454,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
         ubase = __shfl_sync(FULL, ubase, 0);
         if ((int64_t)ubase >= n_work)
             break;
-        const int64_t w = (int64_t)ubase + grp;
-        int seq[1];
-        seq[0] = w < n_work ? (p.order ? p.order[w] : (int)w) : -1;
-        const int64_t start = seq[0] >= 0 ? p.off[seq[0]] : 0;
-        const int len = seq[0] >= 0 ? (int)(p.off[seq[0] + 1] - start) : 0;
+        const BatchItem it = batch_item(p, (int64_t)ubase + grp, n_work, n_pieces);
+        int seq[1] = {it.seq};
+        const bool piece[1] = {it.piece};
+        const int64_t start = it.start;
+        const int len = it.len;
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
         if constexpr (ENDS) {
             int er = -1, eq = -1;
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
             const uint32_t mx = split_unit<L, S, D0, LAZY>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
                                                            has_prev, has_next, p.bnd, gl, &lazy_steps);
             if (gl == 0)
-                write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);
+                write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores, piece);
         }
     }
     // j-steps of the correction loop, counted once per warp

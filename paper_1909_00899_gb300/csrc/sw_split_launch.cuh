@@ -29,7 +29,9 @@ int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
     int64_t grid = (int64_t)num_sms * per_sm;
     if (!a.n_work_dev) {
         const int64_t per_block = (BATCH_THREADS / 32) * (32 / L);
-        const int64_t need = (a.n_work + per_block - 1) / per_block;
+        // pieces of long sequences: at most n_work more items
+        const int64_t items = a.pieces ? 2 * a.n_work : a.n_work;
+        const int64_t need = (items + per_block - 1) / per_block;
         if (need < grid)
             grid = need;
     }

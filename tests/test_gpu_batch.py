@@ -91,6 +91,45 @@ def test_long_queries_many_chunks(sw, kind):
         np.testing.assert_array_equal(got, want, err_msg="qlen=%d" % qlen)
 
 
+def _piece_geometry(m, maxM, e):
+    """Pieces of a long sequence for a single-chunk query of length m: the
+    widest span of a positive-scoring local alignment, the piece length and
+    the stride between piece starts (the library's rule)."""
+    span = m + (m * maxM - 1) // e
+    plen = max(2 * span, 2048)
+    return span, plen, plen - span + 1
+
+
+@pytest.mark.parametrize("kind", LANES)
+def test_long_sequences_split_into_pieces(sw, kind):
+    """Short queries against sequences several pieces long: copies of the
+    query planted across piece boundaries (straddling the overlap, at its
+    edges and inside), with and without a horizontal gap, in protein and DNA
+    scoring; beside them ordinary short sequences, empty ones, and long ones
+    with nothing planted.  Scores equal the oracle's on every lane type."""
+    rng = np.random.default_rng(1011)
+    for M, o, e, A, m in ((synth.protein_matrix(rng), 11, 1, 20, 60), (synth.dna_matrix(), 6, 1, 4, 150)):
+        span, plen, stride = _piece_geometry(m, int(M.max()), e)
+        q = synth.residues(rng, m, A)
+        seqs = [synth.residues(rng, int(x), A) for x in rng.integers(0, 400, 30)] + [np.zeros(0, np.uint8)]
+        for k, shift in enumerate((-m // 2, 0, span - m - 1, stride - 1, -1, plen - stride)):
+            L = plen * 3 + 500 + 37 * k
+            ref = synth.residues(rng, L, A)
+            at = (k % 2 + 1) * stride + shift  # near the start of the second or third piece
+            at = min(max(at, 0), L - m - 40)
+            ref[at:at + m] = q
+            if k % 3 == 2:  # a horizontal gap of 25 inside the copy
+                ref = np.concatenate([ref[:at + m // 2], synth.residues(rng, 25, A), ref[at + m // 2:]])
+            seqs.append(ref)
+        seqs.append(synth.residues(rng, plen * 4 + 11, A))  # long, nothing planted
+        db, off = pack_list(seqs)
+        db_d, off_d = db_to_dev(db, off)
+        want = oracle.gotoh_batch(q, db, off, M, o, e)
+        assert (want[-7:-1] >= m // 2).all()  # the planted copies score
+        got = run(sw, kind, q, M, db_d, off_d, o, e)
+        np.testing.assert_array_equal(got, want, err_msg="A=%d m=%d" % (A, m))
+
+
 @pytest.mark.parametrize("kind", LANES)
 def test_gap_adversary_dna(sw, kind):
     """Long query-side insertions (vertical gaps through many segments) with

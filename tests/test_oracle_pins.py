@@ -302,3 +302,51 @@ def test_unknown_residue_all_positive_matrix():
     q = np.array([0, 9, 1], dtype=np.uint8)
     r = np.array([0, 0, 1], dtype=np.uint8)
     assert oracle.gotoh(q, r, M, 5, 1) == 3 + 1 + 2
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_windows_overlapping_by_the_span_keep_the_score(seed):
+    """The score of a query against a long sequence equals the maximum over
+    windows of 2*span columns every span + 1 columns, where span = m +
+    floor((m * max M - 1) / e) bounds the columns of any positive-scoring
+    local alignment (the rule the batch plan splits long sequences by);
+    windows overlapping by less can miss the optimum.  Copies of the query
+    (some with a horizontal gap) are planted across window boundaries."""
+    rng = np.random.default_rng([12, seed])
+    A = 4 if seed % 2 else 20
+    M = synth.dna_matrix() if A == 4 else synth.protein_matrix(rng)
+    o, e = (6, 1 + seed % 3) if A == 4 else (11, 1 + seed % 3)
+    m = int(rng.integers(6, 14))
+    q = synth.residues(rng, m, A)
+    span = m + (m * int(M.max()) - 1) // e
+    plen, stride = 2 * span, span + 1
+    refs = []
+    for k in range(12):
+        ref = synth.residues(rng, 6 * plen + int(rng.integers(0, 50)), A)
+        at = int(rng.integers(1, 5)) * stride + int(rng.integers(-m, span - m))
+        ref[at:at + m] = q
+        if k % 3 == 0:
+            gap = int(rng.integers(1, 6))
+            ref = np.concatenate([ref[:at + m // 2], synth.residues(rng, gap, A), ref[at + m // 2:]])
+        refs.append(ref)
+    for ref in refs:
+        whole = oracle.gotoh(q, ref, M, o, e)
+        starts = list(range(0, max(1, len(ref) - plen + stride), stride))
+        wins = [ref[s:s + plen] for s in starts]
+        assert starts[-1] + plen >= len(ref)
+        assert max(oracle.gotoh(q, w, M, o, e) for w in wins) == whole
+
+
+def test_windows_without_overlap_miss_a_straddling_copy():
+    """The converse check of the span rule: windows that do not overlap cut a
+    copy of the query planted across their boundary, and their maximum falls
+    below the sequence's score (so the overlap is what keeps it exact)."""
+    rng = np.random.default_rng(1213)
+    M = synth.dna_matrix()
+    q = synth.residues(rng, 40, 4)
+    ref = synth.residues(rng, 3000, 4)
+    plen = 1000
+    ref[plen - 20:plen + 20] = q
+    whole = oracle.gotoh(q, ref, M, 6, 1)
+    cut = max(oracle.gotoh(q, ref[s:s + plen], M, 6, 1) for s in range(0, len(ref), plen))
+    assert whole == 40 and cut < whole
