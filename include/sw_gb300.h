@@ -132,12 +132,13 @@ int sw_plan_query(int32_t qlen, int32_t lane_type, int32_t *lanes,
  * runs its segment with a zero F carry, the carry between segments is the
  * max-plus prefix scan over lanes with weight segLen*e per hop, and the
  * correction of H (and of E) is deferred into the next column's pass.
- * When the query fits one chunk of its layout, database sequences longer
- * than max(2*span, 2048) columns, span = m + (m*maxM - 1)/e, are aligned as
- * windows overlapping by span columns (every positive-scoring alignment
- * spans at most that many) and the largest window score is kept: the same
- * scores, without one warp walking the longest sequence alone (e >= 1 and
- * maxM >= 1 only; scratch grows by 17 bytes per sequence).
+ * When the query fits one chunk of at most 1024 positions and
+ * P = max(2*span, 2048) <= 8192, span = m + (m*maxM - 1)/e, database
+ * sequences longer than P columns are aligned as windows of P columns
+ * overlapping by span columns (every positive-scoring alignment spans at
+ * most that many) and the largest window score is kept: the same scores,
+ * without one warp walking the longest sequence alone (e >= 1 and maxM >= 1
+ * only; scratch grows by 17 bytes per sequence).
  *   db_residues  device, concatenated residue codes
  *   db_offsets   device, int64[n_db + 1], offsets[0] = 0, non-decreasing;
  *                sequence k is db_residues[offsets[k] .. offsets[k+1])

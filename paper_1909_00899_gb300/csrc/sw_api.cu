@@ -22,6 +22,11 @@ int launch_batch_i8(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_
 int launch_batch_q16(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_i32_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
 int launch_batch_q16_ends(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+// launches that split long sequences into pieces (layouts of <= 1024 positions)
+int launch_batch_i32_pieces(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_i16_pieces(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_i8_pieces(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st);
+int launch_batch_q16_pieces(const Plan &pl, bool lazy, const BatchArgs &a, int num_sms, cudaStream_t st);
 }  // namespace swg
 
 using swg::Plan;
@@ -266,6 +271,15 @@ int check_align_args(const sw_profile *prof, const uint8_t *db, const int64_t *o
 
 int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cudaStream_t st)
 {
+    if (a.pieces) {
+        if (pl.lane == SW_LANE_I32)
+            return swg::launch_batch_i32_pieces(pl, lazy, a, sms, st);
+        if (pl.lane == SW_LANE_I16X2)
+            return swg::launch_batch_i16_pieces(pl, lazy, a, sms, st);
+        if (pl.lane == SW_LANE_I16X2Q)
+            return swg::launch_batch_q16_pieces(pl, lazy, a, sms, st);
+        return swg::launch_batch_i8_pieces(pl, a, sms, st);
+    }
     if (pl.lane == SW_LANE_I32)
         return swg::launch_batch_i32(pl, lazy, a, sms, st);
     if (pl.lane == SW_LANE_I16X2)
@@ -277,9 +291,14 @@ int launch_plan(const Plan &pl, bool lazy, const swg::BatchArgs &a, int sms, cud
 
 // Splitting of long sequences: pieces of at least this many columns (a
 // short query keeps a few thousand columns of serial work per item), and no
-// splitting when the overlap alone would make pieces longer than the cap.
+// splitting when pieces would be longer than the cap (the span grows with
+// m x max M / e; beyond the cap hardly any database sequence is longer than
+// a piece, and the splitting kernels would only add their per-item cost).
 constexpr int64_t kMinPieceLen = 2048;
-constexpr int64_t kMaxPieceLen = 1 << 20;
+constexpr int64_t kMaxPieceLen = 8192;
+// layouts instantiated for splitting launches: at most this many positions
+// per chunk (longer queries have spans beyond any usual database sequence)
+constexpr int kPieceMaxChunk = 1024;
 
 // pre_order / pre_total: a database handle's persistent length order and
 // residue count (then no order kernels run and nothing is read back).
@@ -349,7 +368,8 @@ int align_impl(const sw_profile *prof, const uint8_t *db, const int64_t *off, in
     // longest sequence alone.  Scores only (end cells and the lazy-F
     // statistics keep whole sequences).
     int32_t piece_len = 0, piece_stride = 0;
-    if (!ends && !lazy_steps && main.C == 1 && (!packed || C32 == 1) && e >= 1 && prof->maxM >= 1) {
+    if (!ends && !lazy_steps && main.C == 1 && (!packed || C32 == 1) && e >= 1 && prof->maxM >= 1 &&
+        main.L * main.S <= kPieceMaxChunk && n_db < (int64_t)swg::PIECE_BIT) {
         const int64_t span = (int64_t)prof->qlen + ((int64_t)prof->qlen * prof->maxM - 1) / e;
         const int64_t plen = std::max<int64_t>(2 * span, kMinPieceLen);
         if (plen <= kMaxPieceLen) {

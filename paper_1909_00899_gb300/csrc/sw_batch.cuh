@@ -309,8 +309,7 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
 // the flag threshold once one of them reached it.
 template <class LT>
 __device__ __forceinline__ void write_scores(typename LT::T mx, const typename LT::K &k, const int *seq,
-                                             bool has_prev, int32_t flag_thresh, int32_t *scores,
-                                             const bool *piece = nullptr)
+                                             bool has_prev, int32_t flag_thresh, int32_t *scores)
 {
     constexpr int CELLS = LT::CELLS;
     int s[CELLS];
@@ -329,42 +328,67 @@ __device__ __forceinline__ void write_scores(typename LT::T mx, const typename L
         if (seq[c] >= 0) {
             if (LT::CROSS && flag)
                 s[c] = max(s[c], flag_thresh);
-            if (piece && piece[c])
-                atomicMax(&scores[seq[c]], s[c]);  // the sequence's best piece
-            else
-                scores[seq[c]] = s[c];
+            scores[seq[c]] = s[c];
         }
     }
 }
 
-// Work item w of a batch launch: a whole database sequence, or one piece of
-// a long one (items [0, n_pieces) when the call splits long sequences).  A
-// sequence that is split is skipped where it comes up whole.
+// write_scores for launches that split long sequences into pieces: an id
+// with PIECE_BIT set is a piece, whose score joins its sequence's by
+// atomicMax (single-chunk launches only, so nothing to combine from an
+// earlier chunk).
+template <class LT>
+__device__ __forceinline__ void write_scores_pieces(typename LT::T mx, const typename LT::K &k, const int *id,
+                                                    int32_t flag_thresh, int32_t *scores)
+{
+    constexpr int CELLS = LT::CELLS;
+    int s[CELLS];
+    bool flag = false;
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+        s[c] = LT::score(mx, c, k);
+        if (id[c] >= 0)
+            flag |= s[c] >= flag_thresh;
+    }
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+        if (id[c] >= 0) {
+            if (LT::CROSS && flag)
+                s[c] = max(s[c], flag_thresh);
+            if (id[c] & PIECE_BIT)
+                atomicMax(&scores[id[c] & ~PIECE_BIT], s[c]);  // the sequence's best piece
+            else
+                scores[id[c]] = s[c];
+        }
+    }
+}
+
+// Work item w of a launch that splits long sequences: items [0, n_pieces)
+// are pieces (id with PIECE_BIT), then the entries of order, skipping the
+// sequences that were split (id -1: nothing to do).
 struct BatchItem {
-    int seq;  // -1: nothing to do
+    int id;
     int64_t start;
     int len;
-    bool piece;
 };
 
 __device__ __forceinline__ BatchItem batch_item(const BatchArgs &p, int64_t w, int64_t n_work, int n_pieces)
 {
-    BatchItem it{-1, 0, 0, false};
+    BatchItem it{-1, 0, 0};
     if (w >= n_work)
         return it;
     if (w < n_pieces) {
         const Piece pc = p.pieces[w];
-        it.seq = pc.seq;
+        it.id = pc.seq | PIECE_BIT;
         it.start = pc.start;
         it.len = pc.len;
-        it.piece = true;
         return it;
     }
     const int64_t k = w - n_pieces;
     const int s = p.order ? p.order[k] : (int)k;
-    if (p.split && p.split[s])
+    if (p.split[s])
         return it;
-    it.seq = s;
+    it.id = s;
     it.start = p.off[s];
     it.len = (int)(p.off[s + 1] - it.start);
     return it;
@@ -398,7 +422,9 @@ __device__ __forceinline__ void stage_profile(typename LT::Elem *dst, int A, int
     }
 }
 
-template <class LT, int L, int S, bool LAZY, bool ENDS = false>
+// PIECES: the launch splits long sequences into pieces (scores only, one
+// chunk); a separate instantiation so that the others stay as they are.
+template <class LT, int L, int S, bool LAZY, bool ENDS = false, bool PIECES = false>
 __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs p)
 {
     using T = typename LT::T;
@@ -426,7 +452,8 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int grp = lane / L;
-    const int n_pieces = p.n_pieces ? *p.n_pieces : 0;
+    static_assert(!(PIECES && ENDS), "pieces: scores only");
+    const int n_pieces = PIECES ? *p.n_pieces : 0;
     const int64_t n_work = (p.n_work_dev ? (int64_t)(*p.n_work_dev) : p.n_work) + n_pieces;
     const int64_t units = (n_work + CELLS - 1) / CELLS;
     const bool has_prev = p.chunk > 0;
@@ -448,15 +475,21 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
         int seq[CELLS];
         int64_t start[CELLS];
         int len[CELLS];
-        bool piece[CELLS];
         int my_n = 0;
 #pragma unroll
         for (int c = 0; c < CELLS; ++c) {
-            const BatchItem it = batch_item(p, unit < units ? unit * CELLS + c : n_work, n_work, n_pieces);
-            seq[c] = it.seq;
-            start[c] = it.start;
-            len[c] = it.len;
-            piece[c] = it.piece;
+            const int64_t w = unit * CELLS + c;
+            if constexpr (PIECES) {
+                const BatchItem it = batch_item(p, unit < units ? w : n_work, n_work, n_pieces);
+                seq[c] = it.id;
+                start[c] = it.start;
+                len[c] = it.len;
+            } else {
+                const bool ok = unit < units && w < n_work;
+                seq[c] = ok ? (p.order ? p.order[w] : (int)w) : -1;
+                start[c] = ok ? p.off[seq[c]] : 0;
+                len[c] = ok ? (int)(p.off[seq[c] + 1] - start[c]) : 0;
+            }
             my_n = max(my_n, len[c]);
         }
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)my_n);
@@ -482,9 +515,12 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_batch_kernel(const BatchArgs
         } else {
             const T mx = striped_unit<LT, L, S, LAZY>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
                                                       has_prev, has_next, p.bnd, gl, lazy_steps);
-            if (gl == 0)
-                write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), seq, has_prev, p.flag_thresh, p.scores,
-                                 piece);
+            if (gl == 0) {
+                if constexpr (PIECES)
+                    write_scores_pieces<LT>(mx, LT::consts(p.o, p.e, S, p.one), seq, p.flag_thresh, p.scores);
+                else
+                    write_scores<LT>(mx, LT::consts(p.o, p.e, S, p.one), seq, has_prev, p.flag_thresh, p.scores);
+            }
         }
     }
     // j-steps of the correction loop, counted once per warp

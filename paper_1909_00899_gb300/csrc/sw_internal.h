@@ -24,6 +24,10 @@ struct Piece {
     int32_t seq;    // the sequence it belongs to
     int32_t len;    // columns
 };
+// In the batch kernels a work item's sequence id with this bit set is a
+// piece of a long sequence (its score is combined by atomicMax); calls that
+// split long sequences keep their ids below 2^30.
+constexpr int PIECE_BIT = 1 << 30;
 
 struct BatchArgs {
     const int8_t *prof;       // raw striped profile of this plan: [C][A][L][S] int8 (M values)

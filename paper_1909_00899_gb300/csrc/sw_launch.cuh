@@ -6,10 +6,10 @@
 
 namespace swg {
 
-template <class LT, int L, int S, bool LAZY, bool ENDS = false>
+template <class LT, int L, int S, bool LAZY, bool ENDS = false, bool PIECES = false>
 int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-    auto kern = sw_batch_kernel<LT, L, S, LAZY, ENDS>;
+    auto kern = sw_batch_kernel<LT, L, S, LAZY, ENDS, PIECES>;
     // alphabet of at most 32 residues + the unknown and the inert rows
     constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
     static std::once_flag once;
@@ -30,7 +30,7 @@ int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
     if (!a.n_work_dev) {
         // no more blocks than there are work units for their warps (pieces
         // of long sequences: at most n_work more items)
-        const int64_t items = a.pieces ? 2 * a.n_work : a.n_work;
+        const int64_t items = PIECES ? 2 * a.n_work : a.n_work;
         const int64_t units = (items + LT::CELLS - 1) / LT::CELLS;
         const int64_t per_block = (BATCH_THREADS / 32) * (32 / L);
         const int64_t need = (units + per_block - 1) / per_block;

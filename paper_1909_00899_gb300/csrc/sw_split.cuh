@@ -403,7 +403,9 @@ struct SplitMinBlocks {
                                              : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
 };
 
-template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false>
+// PIECES: the launch splits long sequences into pieces (scores only, one
+// chunk); a separate instantiation so that the others stay as they are.
+template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false, bool PIECES = false>
 __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::value) sw_split_kernel(const BatchArgs p)
 {
     constexpr int G = 32 / L;
@@ -440,7 +442,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int grp = lane / L;
-    const int n_pieces = p.n_pieces ? *p.n_pieces : 0;
+    static_assert(!(PIECES && ENDS), "pieces: scores only");
+    const int n_pieces = PIECES ? *p.n_pieces : 0;
     const int64_t n_work = (p.n_work_dev ? (int64_t)(*p.n_work_dev) : p.n_work) + n_pieces;
     const bool has_prev = p.chunk > 0;
     const bool has_next = p.chunk + 1 < p.nchunks;
@@ -454,11 +457,20 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
         ubase = __shfl_sync(FULL, ubase, 0);
         if ((int64_t)ubase >= n_work)
             break;
-        const BatchItem it = batch_item(p, (int64_t)ubase + grp, n_work, n_pieces);
-        int seq[1] = {it.seq};
-        const bool piece[1] = {it.piece};
-        const int64_t start = it.start;
-        const int len = it.len;
+        const int64_t w = (int64_t)ubase + grp;
+        int seq[1];
+        int64_t start;
+        int len;
+        if constexpr (PIECES) {
+            const BatchItem it = batch_item(p, w, n_work, n_pieces);
+            seq[0] = it.id;
+            start = it.start;
+            len = it.len;
+        } else {
+            seq[0] = w < n_work ? (p.order ? p.order[w] : (int)w) : -1;
+            start = seq[0] >= 0 ? p.off[seq[0]] : 0;
+            len = seq[0] >= 0 ? (int)(p.off[seq[0] + 1] - start) : 0;
+        }
         const int ncols = (int)__reduce_max_sync(FULL, (unsigned)len);
         if constexpr (ENDS) {
             int er = -1, eq = -1;
@@ -483,8 +495,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
         } else {
             const uint32_t mx = split_unit<L, S, D0, LAZY>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
                                                            has_prev, has_next, p.bnd, gl, &lazy_steps);
-            if (gl == 0)
-                write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores, piece);
+            if (gl == 0) {
+                if constexpr (PIECES)
+                    write_scores_pieces<LaneQ16>(mx, k, seq, p.flag_thresh, p.scores);
+                else
+                    write_scores<LaneQ16>(mx, k, seq, has_prev, p.flag_thresh, p.scores);
+            }
         }
     }
     // j-steps of the correction loop, counted once per warp

@@ -7,10 +7,10 @@
 
 namespace swg {
 
-template <int L, int S, bool D0, bool LAZY, bool ENDS = false>
+template <int L, int S, bool D0, bool LAZY, bool ENDS = false, bool PIECES = false>
 int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
-    auto kern = sw_split_kernel<L, S, D0, LAZY, ENDS>;
+    auto kern = sw_split_kernel<L, S, D0, LAZY, ENDS, PIECES>;
     constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, 4>::value * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -30,7 +30,7 @@ int launch_split_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
     if (!a.n_work_dev) {
         const int64_t per_block = (BATCH_THREADS / 32) * (32 / L);
         // pieces of long sequences: at most n_work more items
-        const int64_t items = a.pieces ? 2 * a.n_work : a.n_work;
+        const int64_t items = PIECES ? 2 * a.n_work : a.n_work;
         const int64_t need = (items + per_block - 1) / per_block;
         if (need < grid)
             grid = need;
@@ -61,6 +61,28 @@ int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStrea
     SWG_CASE(64, 20)
     SWG_CASE(64, 24)
     SWG_CASE(64, 32)
+#undef SWG_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+// Launches that split long sequences into pieces (scores, scan-F or
+// lazy-F): the layouts of at most 1024 query positions, the only ones a
+// splitting call uses.
+template <bool LAZY>
+int launch_split_plan_pieces(const Plan &pl, const BatchArgs &a, int num_sms, cudaStream_t st)
+{
+    const bool d0 = a.min_m >= -a.o;
+#define SWG_CASE(VL, SS)                                                                          \
+    if (pl.L == VL && pl.S == SS)                                                                 \
+        return d0 ? launch_split_inst<VL / 2, SS, true, LAZY, false, true>(a, num_sms, st)        \
+                  : launch_split_inst<VL / 2, SS, false, LAZY, false, true>(a, num_sms, st);
+    SWG_CASE(2, 16)
+    SWG_CASE(2, 32)
+    SWG_CASE(16, 8)
+    SWG_CASE(32, 8)
+    SWG_CASE(32, 16)
+    SWG_CASE(64, 8)
+    SWG_CASE(64, 16)
 #undef SWG_CASE
     return (int)cudaErrorInvalidValue;
 }
