@@ -56,6 +56,7 @@ int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStrea
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
     SWG_CASE(32, 16)
+    SWG_CASE(32, 32)
     SWG_CASE(64, 8)
     SWG_CASE(64, 16)
     SWG_CASE(64, 20)
@@ -81,6 +82,7 @@ int launch_split_plan_pieces(const Plan &pl, const BatchArgs &a, int num_sms, cu
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
     SWG_CASE(32, 16)
+    SWG_CASE(32, 32)
     SWG_CASE(64, 8)
     SWG_CASE(64, 16)
 #undef SWG_CASE
