@@ -55,7 +55,10 @@ int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStrea
     SWG_CASE(2, 32)
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
+    SWG_CASE(32, 12)
     SWG_CASE(32, 16)
+    SWG_CASE(32, 20)
+    SWG_CASE(32, 24)
     SWG_CASE(32, 32)
     SWG_CASE(64, 8)
     SWG_CASE(64, 16)
@@ -81,7 +84,10 @@ int launch_split_plan_pieces(const Plan &pl, const BatchArgs &a, int num_sms, cu
     SWG_CASE(2, 32)
     SWG_CASE(16, 8)
     SWG_CASE(32, 8)
+    SWG_CASE(32, 12)
     SWG_CASE(32, 16)
+    SWG_CASE(32, 20)
+    SWG_CASE(32, 24)
     SWG_CASE(32, 32)
     SWG_CASE(64, 8)
     SWG_CASE(64, 16)
