@@ -206,6 +206,11 @@ int sw_align_db(const sw_profile *prof, const sw_db *db, int32_t gap_open,
 int sw_align_lazyf_db(const sw_profile *prof, const sw_db *db,
                       int32_t gap_open, int32_t gap_extend,
                       int32_t *scores_out, void *cuda_stream);
+/* sw_align_db_ends — sw_align_batch_ends against a resident database (same
+ * outputs: q_end_out, r_end_out device int32[n], -1 where the score is 0). */
+int sw_align_db_ends(const sw_profile *prof, const sw_db *db, int32_t gap_open,
+                     int32_t gap_extend, int32_t *scores_out, int32_t *q_end_out,
+                     int32_t *r_end_out, void *cuda_stream);
 
 /*
  * sw_align_pairs — n_pairs independent alignments, pair k aligning query

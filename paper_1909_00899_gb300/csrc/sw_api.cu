@@ -753,6 +753,17 @@ int sw_align_db(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32
                       db->order, db->total);
 }
 
+int sw_align_db_ends(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32_t gap_extend,
+                     int32_t *scores_out, int32_t *q_end_out, int32_t *r_end_out, void *cuda_stream)
+{
+    if (!db)
+        return fail(SW_ERR_INVALID, "db is NULL");
+    if (db->n > 0 && (!q_end_out || !r_end_out))
+        return fail(SW_ERR_INVALID, "q_end_out / r_end_out is NULL");
+    return align_impl(prof, db->res, db->off, db->n, gap_open, gap_extend, scores_out, cuda_stream, false,
+                      db->order, db->total, nullptr, db->n > 0 ? q_end_out : nullptr, r_end_out);
+}
+
 int sw_align_lazyf_db(const sw_profile *prof, const sw_db *db, int32_t gap_open, int32_t gap_extend,
                       int32_t *scores_out, void *cuda_stream)
 {

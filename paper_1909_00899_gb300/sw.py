@@ -29,11 +29,12 @@ SW_LANE_I16X2Q = 4
 
 # every function declared in include/sw_gb300.h
 EXPORTS = (
-    "sw_profile_build", "sw_profile_build_ex", "sw_profile_free", "sw_profile_free_async", "sw_profile_plan", "sw_align_batch",
-    "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
+    "sw_profile_build", "sw_profile_build_ex", "sw_profile_free", "sw_profile_free_async", "sw_profile_plan",
+    "sw_align_batch", "sw_align_lazyf_batch", "sw_align_pairs", "sw_stream_sync", "sw_last_error",
     "sw_probe_cell_rate", "sw_probe_cell_rate_pass", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
-    "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats", "sw_align_batch_noalloc",
-    "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends", "sw_align_lazyf_pairs_lane",
+    "sw_align_db_ends", "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats",
+    "sw_align_batch_noalloc", "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends",
+    "sw_align_lazyf_pairs_lane",
 )
 
 
@@ -87,6 +88,8 @@ def lib():
             f = getattr(L, name)
             f.restype = ctypes.c_int
             f.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
+        L.sw_align_db_ends.restype = ctypes.c_int
+        L.sw_align_db_ends.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp]
         L.sw_align_lazyf_pairs.restype = ctypes.c_int
         L.sw_align_lazyf_pairs.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp]
         L.sw_align_lazyf_pairs_lane.restype = ctypes.c_int
@@ -316,6 +319,17 @@ def sw_align_db(profile, db, gap_open, gap_extend, scores_out, stream=None):
     _check(lib().sw_align_db(profile.handle, db.handle, int(gap_open), int(gap_extend),
                              _dev_ptr(scores_out, "int32"), _stream(stream)))
     return scores_out
+
+
+def sw_align_db_ends(profile, db, gap_open, gap_extend, scores_out, q_end_out, r_end_out, stream=None):
+    """Scores and end cells against a resident database (as sw_align_batch_ends)."""
+    for t in (scores_out, q_end_out, r_end_out):
+        if t.numel() < db.n:
+            raise ValueError("output too small")
+    _check(lib().sw_align_db_ends(profile.handle, db.handle, int(gap_open), int(gap_extend),
+                                  _dev_ptr(scores_out, "int32"), _dev_ptr(q_end_out, "int32"),
+                                  _dev_ptr(r_end_out, "int32"), _stream(stream)))
+    return scores_out, q_end_out, r_end_out
 
 
 def sw_align_lazyf_db(profile, db, gap_open, gap_extend, scores_out, stream=None):

@@ -58,10 +58,19 @@ def test_db_handle_matches_batch_and_oracle(sw, small_db):
         sw.sw_align_batch(prof, db_d, off_d, 11, 1, b)
         prof32 = sw.Profile(q, M, sw.SW_LANE_I32)
         sw.sw_align_lazyf_db(prof32, h, 11, 1, c)
+        # end cells against the handle equal the oracle's
+        sc = torch.empty(h.n, dtype=torch.int32, device="cuda")
+        qe = torch.empty(h.n, dtype=torch.int32, device="cuda")
+        re_ = torch.empty(h.n, dtype=torch.int32, device="cuda")
+        sw.sw_align_db_ends(prof, h, 11, 1, sc, qe, re_)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(a.cpu().numpy(), want)
         np.testing.assert_array_equal(b.cpu().numpy(), want)
         np.testing.assert_array_equal(c.cpu().numpy(), want)
+        ws, wq, wr = oracle.gotoh_end_batch(q, db, off, M, 11, 1)
+        np.testing.assert_array_equal(sc.cpu().numpy(), ws)
+        np.testing.assert_array_equal(qe.cpu().numpy(), wq)
+        np.testing.assert_array_equal(re_.cpu().numpy(), wr)
     h.free()
 
 
