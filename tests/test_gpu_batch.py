@@ -130,6 +130,31 @@ def test_long_sequences_split_into_pieces(sw, kind):
         np.testing.assert_array_equal(got, want, err_msg="A=%d m=%d" % (A, m))
 
 
+@pytest.mark.parametrize("kind", ["auto", "i32", "i16x2", "lazyf16q"])
+def test_piece_slots_run_out(sw, kind):
+    """More pieces than slots (at most one per database sequence): a few long
+    sequences with a planted copy each, among fewer short ones, so that some
+    long sequences must stay whole.  Every score equals the oracle's, split
+    or not."""
+    rng = np.random.default_rng(1012)
+    M, o, e, m = synth.protein_matrix(rng), 11, 1, 60
+    span, plen, stride = _piece_geometry(m, int(M.max()), e)
+    q = synth.residues(rng, m, 20)
+    seqs = []
+    for k in range(4):  # 4 long sequences of 3-4 pieces each, 2 short ones: 6 slots
+        ref = synth.residues(rng, plen + stride * (2 + k % 2) + 17 * k, 20)
+        at = stride * (1 + k % 2) - m // 3
+        ref[at:at + m] = q
+        seqs.append(ref)
+    seqs += [synth.residues(rng, 90, 20), synth.residues(rng, 5, 20)]
+    db, off = pack_list(seqs)
+    db_d, off_d = db_to_dev(db, off)
+    want = oracle.gotoh_batch(q, db, off, M, o, e)
+    assert (want[:4] >= 4 * m).all()
+    got = run(sw, kind, q, M, db_d, off_d, o, e)
+    np.testing.assert_array_equal(got, want)
+
+
 @pytest.mark.parametrize("kind", LANES)
 def test_gap_adversary_dna(sw, kind):
     """Long query-side insertions (vertical gaps through many segments) with
