@@ -97,7 +97,7 @@ int sw_profile_build(const uint8_t *query, int32_t qlen,
  * scan), s16x2 {8x8, 8x16, 16x8, 16x16, 32x8, 32x12, 32x16, 16x32,
  * 32x24, 32x32}, s8x4 {8x16, 16x16, 32x16}, split s16x2 (virtual lanes)
  * {2x16, 2x32, 16x8, 32x8, 32x12, 32x16, 32x20, 32x24, 32x32, 64x8, 64x16,
- * 64x20, 64x24, 64x32} (2
+ * 64x20, 64x24, 64x28, 64x32} (2
  * virtual lanes: one thread per alignment).  Used by the autotuner.
  */
 int sw_profile_build_ex(const uint8_t *query, int32_t qlen,

@@ -112,7 +112,7 @@ const Choice kAllI32[] = {{1, 16}, {1, 32}, {4, 8},   {4, 32},  {8, 8},  {8, 16}
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
 const Choice kAllQ16[] = {{2, 16}, {2, 32}, {16, 8}, {32, 8}, {32, 12}, {32, 16}, {32, 20}, {32, 24}, {32, 32},
-                          {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 32}};
+                          {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 28}, {64, 32}};
 
 bool plan_supported(int lane, int L, int S)
 {
@@ -120,7 +120,7 @@ bool plan_supported(int lane, int L, int S)
                       : lane == SW_LANE_I16X2 ? kAllI16
                       : lane == SW_LANE_I8X4  ? kAllI8
                                               : kAllQ16;
-    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 14);
+    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 15);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;
@@ -149,7 +149,7 @@ const AutoChoice kAuto[] = {
     {SW_LANE_I16X2Q, 32, 12, 4136}, {SW_LANE_I16X2Q, 32, 20, 4951}, {SW_LANE_I16X2Q, 32, 24, 4921},
     {SW_LANE_I16X2Q, 32, 32, 4900},
     {SW_LANE_I16X2Q, 64, 8, 3956},  {SW_LANE_I16X2Q, 64, 16, 4808}, {SW_LANE_I16X2Q, 64, 20, 5030},
-    {SW_LANE_I16X2Q, 64, 24, 5030}, {SW_LANE_I16X2Q, 64, 32, 5130}, {SW_LANE_I16X2, 32, 16, 3865},
+    {SW_LANE_I16X2Q, 64, 24, 5030}, {SW_LANE_I16X2Q, 64, 28, 4893}, {SW_LANE_I16X2Q, 64, 32, 5130}, {SW_LANE_I16X2, 32, 16, 3865},
     {SW_LANE_I16X2, 32, 32, 4578},
 };
 constexpr double kChunkCost = 0.015;

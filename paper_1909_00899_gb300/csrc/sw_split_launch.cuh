@@ -64,6 +64,7 @@ int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStrea
     SWG_CASE(64, 16)
     SWG_CASE(64, 20)
     SWG_CASE(64, 24)
+    SWG_CASE(64, 28)
     SWG_CASE(64, 32)
 #undef SWG_CASE
     return (int)cudaErrorInvalidValue;
