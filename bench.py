@@ -406,8 +406,14 @@ def main():
         plans.append(pl)
         packed = pl["lane_type"] != sw.SW_LANE_I32
         # profile build (+ its int32 twin), 3 order kernels, one launch per
-        # chunk, then for packed lanes the flag kernel and the int32 rescore
-        launches_per_step += (2 if packed else 1) + 3 + pl["chunks"] + ((1 + pl32["chunks"]) if packed else 0)
+        # chunk, then for packed lanes the flag kernel and the int32 rescore;
+        # a short one-chunk query also plans the windows of long sequences
+        # (the library's rule: pieces of max(2 span, 2048) <= 8192 columns)
+        span = m + (m * int(M.max()) - 1) // e
+        windows = (pl["chunks"] == 1 and (not packed or pl32["chunks"] == 1) and e >= 1 and int(M.max()) >= 1
+                   and pl["lanes"] * pl["seg_len"] <= 1024 and max(2 * span, 2048) <= 8192)
+        launches_per_step += ((2 if packed else 1) + 3 + pl["chunks"] + ((1 + pl32["chunks"]) if packed else 0)
+                              + (1 if windows else 0))
     i_dom = QLENS.index(max(QLENS))
     plan = plans[i_dom]
     cells_per_op = {1: 1, 2: 2, 3: 4, 4: 2}[plan["lane_type"]]
