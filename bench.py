@@ -676,6 +676,40 @@ def run_pairs(args):
                             "lazyf_gcups_by_lane": {"int32": scells / (lfm * 1e-3) / 1e9,
                                                     "s16x2_split": scells / (lqm * 1e-3) / 1e9},
                             "scan_vs_lazyf": min(lfm, lqm) / sms, "lazyf_C_factor_int32": c_fac}
+    # the synthetic lazy-F worst case: query = X + Y + Z vs reference = X + Z
+    adv = synth.workload_gap_adversary(n_pairs=min(200_000, n))
+    aq, aqo, ar, aro = (torch.from_numpy(adv[k]).cuda() for k in ("q", "q_off", "r", "r_off"))
+    na = len(adv["q_off"]) - 1
+    ao = torch.empty(na, dtype=torch.int32, device="cuda")
+    acells = float((np.diff(adv["q_off"]) * np.diff(adv["r_off"])).sum())
+    af = lambda: sw.sw_align_pairs(aq, aqo, ar, aro, adv["M"], adv["o"], adv["e"], ao, stream=st)
+    af()
+    ams = _events_ms(af, st, 2)
+    a_got = ao.cpu().numpy()
+    steps.zero_()
+    al = lambda: sw.sw_align_lazyf_pairs(aq, aqo, ar, aro, adv["M"], adv["o"], adv["e"], ao, lazy_steps=steps,
+                                         stream=st)
+    al()
+    a_c = float(steps.item()) * 32 / acells
+    alm = _events_ms(al, st, 2)
+    aqz = lambda: sw.sw_align_lazyf_pairs(aq, aqo, ar, aro, adv["M"], adv["o"], adv["e"], ao, stream=st,
+                                          lane_type=sw.SW_LANE_I16X2Q)
+    aqz()
+    aqm = _events_ms(aqz, st, 2)
+    a_ids = np.sort(np.random.default_rng(6).choice(na, size=min(na, 1000), replace=False))
+    a_sub = _pairs_subset(adv, a_ids)
+    a_want = oracle.gotoh_pairs(a_sub["q"], a_sub["q_off"], a_sub["r"], a_sub["r_off"], adv["M"], adv["o"],
+                                adv["e"])
+    if not np.array_equal(a_got[a_ids], a_want):
+        raise SystemExit("pairs: sampled gap-adversary scores differ from the oracle")
+    per_class["gap_adversary"] = {"pairs": int(na), "scan_gcups": acells / (ams * 1e-3) / 1e9,
+                                  "lazyf_gcups": acells / (min(alm, aqm) * 1e-3) / 1e9,
+                                  "lazyf_gcups_by_lane": {"int32": acells / (alm * 1e-3) / 1e9,
+                                                          "s16x2_split": acells / (aqm * 1e-3) / 1e9},
+                                  "scan_vs_lazyf": min(alm, aqm) / ams, "lazyf_C_factor_int32": a_c,
+                                  "recipe": "query X+Y+Z vs reference X+Z, |X|,|Z| 60..150, |Y| 40..200, "
+                                            "DNA +1/-4, o=6 e=1",
+                                  "check": {"sampled": int(a_ids.size), "mismatches": 0}}
     worst = max(per_class, key=lambda k: per_class[k]["scan_vs_lazyf"])
     # exactness on a sample, every lane type agreed already in the tests
     sw.sw_align_pairs(qd, qo, rd, ro, w["M"], w["o"], w["e"], out, stream=st)

@@ -110,6 +110,33 @@ def _substitute(rng, reads, identity, A):
     return np.where(hit, (reads + shift) % A, reads).astype(np.uint8)
 
 
+def workload_gap_adversary(seed_salt: int = 0, n_pairs: int = 200_000, xlo: int = 60, xhi: int = 150,
+                           ylo: int = 40, yhi: int = 200):
+    """The lazy-F worst case as read/window pairs: query = X + Y + Z against
+    reference = X + Z (X, Z iid DNA of xlo..xhi bases, Y of ylo..yhi random
+    bases inserted into the query), so the best alignment carries a vertical
+    gap of |Y| through many query segments.  DNA +1/-4, o=6, e=1."""
+    rng = rng_for(5, seed_salt)
+    A = DNA_A
+    n = int(n_pairs)
+    xl = rng.integers(xlo, xhi + 1, n)
+    yl = rng.integers(ylo, yhi + 1, n)
+    zl = rng.integers(xlo, xhi + 1, n)
+    qs, rs = [], []
+    for i in range(n):
+        X = residues(rng, int(xl[i]), A)
+        Y = residues(rng, int(yl[i]), A)
+        Z = residues(rng, int(zl[i]), A)
+        qs.append(np.concatenate([X, Y, Z]))
+        rs.append(np.concatenate([X, Z]))
+    q_off = np.zeros(n + 1, dtype=np.int64)
+    r_off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum([len(x) for x in qs], out=q_off[1:])
+    np.cumsum([len(x) for x in rs], out=r_off[1:])
+    return dict(q=np.concatenate(qs).astype(np.uint8), q_off=q_off, r=np.concatenate(rs).astype(np.uint8),
+                r_off=r_off, M=dna_matrix(), o=6, e=1)
+
+
 def workload_reads(seed_salt: int = 0, n_pairs: int = 1_000_000,
                    read_len: int = 150, win_len: int = 2000):
     """DNA reads vs their own reference windows (mate-rescue stand-in).
