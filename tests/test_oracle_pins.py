@@ -350,3 +350,22 @@ def test_windows_without_overlap_miss_a_straddling_copy():
     whole = oracle.gotoh(q, ref, M, 6, 1)
     cut = max(oracle.gotoh(q, ref[s:s + plen], M, 6, 1) for s in range(0, len(ref), plen))
     assert whole == 40 and cut < whole
+
+
+def test_gap_adversary_workload_is_what_it_claims():
+    """The lazy-F worst-case workload: every query is X + Y + Z and its
+    reference X + Z (|X|, |Z| >= 60, |Y| in 40..200), so the oracle's score is
+    at least that of aligning X and Z across one vertical gap of |Y|
+    (|X| + |Z| - o - (|Y| - 1) e) and at least the longer of X and Z alone."""
+    w = synth.workload_gap_adversary(n_pairs=40)
+    M, o, e = w["M"], w["o"], w["e"]
+    q, qo, r, ro = w["q"], w["q_off"], w["r"], w["r_off"]
+    for i in range(40):
+        qi, ri = q[qo[i]:qo[i + 1]], r[ro[i]:ro[i + 1]]
+        y = len(qi) - len(ri)
+        assert 40 <= y <= 200
+        pre = next((k for k in range(len(ri)) if qi[k] != ri[k]), len(ri))
+        suf = next((k for k in range(len(ri)) if qi[len(qi) - 1 - k] != ri[len(ri) - 1 - k]), len(ri))
+        assert pre >= 60 and suf >= 60  # X and Z are shared (at least)
+        s = oracle.gotoh(qi, ri, M, o, e)
+        assert s >= max(len(ri) - o - (y - 1) * e, pre, suf)  # an exact common run of k scores k
