@@ -87,6 +87,13 @@ def test_plan_query_covers_the_query_host_only(swlib):
     assert picks[512] == dict(lanes=32, seg_len=16, chunks=1, lane_type=4)
     assert picks[2048] == dict(lanes=64, seg_len=32, chunks=1, lane_type=4)
     assert picks[5000] == dict(lanes=64, seg_len=20, chunks=4, lane_type=4)
+    # lengths between the benchmark's: the layout whose chunk the query fills
+    # best at its measured rate (16 threads x 12/20/24/32, 32 threads x 28)
+    mids = {300: (32, 12, 1), 600: (32, 20, 1), 700: (32, 24, 1), 1000: (32, 32, 1), 1700: (64, 28, 1),
+            3500: (64, 28, 2)}
+    for m, (lanes, seg, chunks) in mids.items():
+        assert swlib.sw_plan_query(m) == dict(lanes=lanes, seg_len=seg, chunks=chunks, lane_type=4), m
+        assert m / (chunks * lanes * seg) > 0.75
     with pytest.raises(swlib.SwError):
         swlib.sw_plan_query(-1)
     with pytest.raises(swlib.SwError):
