@@ -28,14 +28,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 QLENS = (128, 512, 2048, 5000)
-# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
-# capture summarised in profiles/sw_batch_kernel_s16x2_32x32_m2048_100k.md
-# (chunk 0 of an m=2048 query against this database).  Set to None whenever
-# the kernel changes, until it is captured again.
-NCU_TRAFFIC = {"bytes_per_launch": 48.484608e6 + 267.697920e6,
-               "kernel": "sw_split_kernel<32, 20, true, false, false>", "launch": "m=5000 chunk 0 vs 100k sequences",
-               "source": "profiles/sw_split_kernel_q16_32x20_m5000_100k.md"}
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
+# capture of that launch; None while the kernel has changed since then.
+NCU_TRAFFIC = None
 METRIC = "GCUPS scan-F (bit-exact) vs lazy-F"
+PROBE_ITERS = 1 << 19  # plain-pass probe: about 0.5 s on every SM
 WORKLOAD = ("protein queries m in {128,512,2048,5000} vs 100k db seqs, log-normal lengths "
             "(median 300, sigma 0.76, clip [20,35000]), o=11 e=1")
 
@@ -425,16 +422,31 @@ def main():
     kernel_gcups = QLENS[i_dom] * total_res / (per_q[i_dom] * 1e-3) / 1e9
     d0 = int(M.min()) >= -o
     if plan["lane_type"] == sw.SW_LANE_I16X2Q:
-        kname = "sw_split_kernel<%d, %d, %s, false, false>" % (plan["lanes"] // 2, plan["seg_len"],
-                                                               "true" if d0 else "false")
+        # template <threads, segment, D0, LAZY, ENDS, PIECES, AC>; the
+        # always-corrected pass on the layouts the library runs it on
+        ac = d0 and plan["lanes"] >= 16 and plan["seg_len"] not in (12, 20)
+        kname = "sw_split_kernel<%d, %d, %s, false, false, false, %s>" % (
+            plan["lanes"] // 2, plan["seg_len"], "true" if d0 else "false", "true" if ac else "false")
     else:
         kname = "sw_batch_kernel<lane %d, %d, %d, false, false>" % (plan["lane_type"], plan["lanes"],
                                                                     plan["seg_len"])
-    probe = None if args.quick else sw.sw_probe_cell_rate(plan["lane_type"], 4096) / 1e9
-    # the same for the pass the dominant kernel runs in nearly every column
-    # here: the shorter corrected pass (every score >= -o, a carry arrives)
-    probe_corr = (None if args.quick or not d0 or plan["lane_type"] == sw.SW_LANE_I8X4
-                  else sw.sw_probe_cell_rate_pass(plan["lane_type"], 1, 4096) / 1e9)
+    # The roofline's peak: the measured cell rate of the plain pass (the
+    # per-cell instruction sequence with no correction, scan, loads or
+    # shuffles) on the dominant kernel's lane type across every SM, timed
+    # long enough (about 0.5 s) to carry its own clock record.  The
+    # correction and scan the method adds count against the kernel, not in
+    # the denominator.  The unit-count figure is kept as peak_model.
+    psampler = ClockSampler(local)
+    psampler.start()
+    probe = sw.sw_probe_cell_rate(plan["lane_type"], PROBE_ITERS) / 1e9
+    probe_clocks = psampler.stop()
+    # informative: the corrected passes' own ceilings (the shorter corrected
+    # pass, and the always-corrected pass the long-query kernels run)
+    probe_corr = probe_ac = None
+    if not args.quick and d0 and plan["lane_type"] != sw.SW_LANE_I8X4:
+        probe_corr = sw.sw_probe_cell_rate_pass(plan["lane_type"], 1, PROBE_ITERS // 4) / 1e9
+        if plan["lane_type"] == sw.SW_LANE_I16X2Q:
+            probe_ac = sw.sw_probe_cell_rate_pass(plan["lane_type"], 2, PROBE_ITERS // 4) / 1e9
 
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
@@ -454,21 +466,31 @@ def main():
         "scan_int32": scan_i32,
         "scan_vs_lazyf_per_query": ({str(m): (m * total_res / (t * 1e-3) / 1e9) / lazy["per_query_gcups"][str(m)]
                                      for m, t in zip(QLENS, per_q)} if lazy else None),
-        "roofline": {"bound": "alu", "achieved": kernel_gcups, "peak": peak_alu, "unit": "GCUPS",
-                     "frac": kernel_gcups / peak_alu, "kernel": kname,
+        "roofline": {"bound": "alu", "achieved": kernel_gcups, "peak": probe, "unit": "GCUPS",
+                     "frac": kernel_gcups / probe, "kernel": kname,
                      "launches_per_call": plan["chunks"], "ms_per_launch": per_q[i_dom] / max(1, plan["chunks"]),
                      "cells_per_launch": QLENS[i_dom] * total_res / max(1, plan["chunks"]),
                      "traffic": NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC else None,
                      "traffic_basis": NCU_TRAFFIC,
-                     "peak_basis": ("%d SMs x 64 int lane-ops/clk (half-rate ALU pipe, 4 x 16 lanes) x %.0f MHz "
-                                    "(median sampled) / %g DPX instr per cell" % (sms, mhz, 6.0 / cells_per_op)),
+                     "peak_basis": ("measured: sw_probe_cell_rate, the plain-pass cell sequence of lane type %d "
+                                    "(h, H - o, X, E, F, running max; no correction, scan, loads or shuffles) on "
+                                    "every SM, %d iterations, clocks in probe_clocks" % (plan["lane_type"],
+                                                                                       PROBE_ITERS)),
+                     "probe_clocks": probe_clocks,
+                     "peak_model": peak_alu, "frac_of_model": kernel_gcups / peak_alu,
+                     "peak_model_basis": ("unit counts, not a ceiling: %d SMs x 64 int lane-ops/clk (half-rate ALU "
+                                          "pipe, 4 x 16 lanes) x %.0f MHz (median sampled) / %g instr per cell "
+                                          "(6 per register, all on the ALU pipe; the kernels issue the additions "
+                                          "on the FMA pipe, so the measured probe runs above it)"
+                                          % (sms, mhz, 6.0 / cells_per_op)),
                      "achieved_basis": ("m*n of the m=%d call (its %d launches of the kernel; profile, order, "
                                         "flag and rescore launches < 0.2 %%) / its CUDA-event time on the "
                                         "launching stream" % (QLENS[i_dom], plan["chunks"])),
-                     "achieved_all_queries": all_gcups, "frac_all_queries": all_gcups / peak_alu,
-                     "probe_gcups": probe, "frac_of_probe": (kernel_gcups / probe) if probe else None,
+                     "achieved_all_queries": all_gcups, "frac_all_queries": all_gcups / probe,
                      "probe_corrected_gcups": probe_corr,
-                     "frac_of_probe_corrected": (kernel_gcups / probe_corr) if probe_corr else None},
+                     "frac_of_probe_corrected": (kernel_gcups / probe_corr) if probe_corr else None,
+                     "probe_always_corrected_gcups": probe_ac,
+                     "frac_of_probe_always_corrected": (kernel_gcups / probe_ac) if probe_ac else None},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

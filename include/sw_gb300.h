@@ -140,6 +140,13 @@ int sw_plan_query(int32_t qlen, int32_t lane_type, int32_t *lanes,
  * most that many) and the largest window score is kept: the same scores,
  * without one warp walking the longest sequence alone (e >= 1 and maxM >= 1
  * only; scratch grows by 17 bytes per sequence).
+ * Synchronisation: when the query spans more than one chunk (of the
+ * profile's layout, or of the int32 layout a packed profile rescores with:
+ * above 1024 positions), the chunk boundary rows are sized by the residue
+ * count, so the call reads db_offsets[n_db] back and synchronises
+ * cuda_stream first; such a call cannot be captured into a CUDA graph.
+ * sw_db_create caches that count once: sw_align_db on the handle never
+ * synchronises and can be captured for any query length.
  *   db_residues  device, concatenated residue codes
  *   db_offsets   device, int64[n_db + 1], offsets[0] = 0, non-decreasing;
  *                sequence k is db_residues[offsets[k] .. offsets[k+1])
@@ -310,7 +317,17 @@ int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
  *    clears the counters it needs on its stream.
  *  - The first call on a device looks the array's address up
  *    (cudaGetSymbolAddress) with that device current; make it before any
- *    stream capture.
+ *    stream capture.  The address is kept for the process: after
+ *    cudaDeviceReset (or a release of the device's primary context) the
+ *    module, and with it the array, moves, so the call must not be used on
+ *    that device again.
+ *  - A query longer than one chunk synchronises cuda_stream on every call
+ *    (as sw_align_batch does: the boundary rows are sized by reading
+ *    db_offsets[n_db] back), so such calls can never be captured.
+ *  - Long database sequences are not split into overlapping windows (the
+ *    window plan would need scratch per sequence), so a short query against
+ *    a few very long sequences can take longer than with sw_align_batch:
+ *    one warp walks each of them whole.  Scores are the same.
  */
 #define SW_NOALLOC_SCRATCH_BYTES (32u << 20)
 int sw_align_batch_noalloc(const sw_profile *prof, const uint8_t *db_residues,
@@ -344,8 +361,11 @@ int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_secon
  * is the shorter corrected pass the kernels run in columns that receive a
  * carry when every substitution score is >= -gap_open (the deferred
  * correction of Alg. 6: the diagonal and E raised by the carry, decaying by
- * gap_extend per position).  SW_LANE_I8X4 has no corrected pass
- * (SW_ERR_INVALID), as has any other value of corrected.
+ * gap_extend per position); corrected = 2 (SW_LANE_I16X2 / _I16X2Q only)
+ * is the always-corrected pass of the long-query split kernels (no carry
+ * vote, the zero floor of H taken on the corrected diagonal).
+ * SW_LANE_I8X4 has no corrected pass (SW_ERR_INVALID), as has any other
+ * value of corrected.
  */
 int sw_probe_cell_rate_pass(int32_t lane_type, int32_t corrected, int32_t iters,
                             double *cells_per_second, void *cuda_stream);

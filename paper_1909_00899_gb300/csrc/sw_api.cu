@@ -111,8 +111,8 @@ const Choice kAllI32[] = {{1, 16}, {1, 32}, {4, 8},   {4, 32},  {8, 8},  {8, 16}
                           {16, 16}, {32, 8}, {32, 12}, {32, 16}, {8, 32}, {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
-const Choice kAllQ16[] = {{2, 16}, {2, 32}, {16, 8}, {32, 8}, {32, 12}, {32, 16}, {32, 20}, {32, 24}, {32, 32},
-                          {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 28}, {64, 32}};
+const Choice kAllQ16[] = {{2, 16}, {2, 32}, {16, 8},  {32, 8},  {32, 12}, {32, 16}, {32, 20}, {32, 24}, {32, 32},
+                          {32, 40}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 28}, {64, 32}, {64, 40}};
 
 bool plan_supported(int lane, int L, int S)
 {
@@ -120,7 +120,7 @@ bool plan_supported(int lane, int L, int S)
                       : lane == SW_LANE_I16X2 ? kAllI16
                       : lane == SW_LANE_I8X4  ? kAllI8
                                               : kAllQ16;
-    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 15);
+    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 17);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;
@@ -136,21 +136,23 @@ const int kPairI32N = 6, kPairI16N = 5, kPairI8N = 4, kPairQ16N = 5;
 
 // Automatic choice of lane type and layout: the layout maximising
 // its measured single-chunk rate on GB300 (GCUPS per processed cell, 100k
-// log-normal protein sequences; refined per workload by the autotuner)
-// x (useful positions / chunk positions) / (1 + 1.5 % per extra chunk: each
-// chunk launch re-streams the database, hands boundary rows on and drains
-// its own tail).
+// log-normal protein sequences, the query as long as one chunk; the
+// split layouts with the always-corrected pass where it runs; 32 x 40 and
+// 64 x 40 from their multi-chunk runs at m = 5000; refined per workload by
+// the autotuner) x (useful positions / chunk positions) / (1 + 1.5 % per
+// extra chunk: each chunk launch re-streams the database, hands boundary
+// rows on and drains its own tail).
 struct AutoChoice {
     int lane, L, S;
     double gcups;
 };
 const AutoChoice kAuto[] = {
-    {SW_LANE_I16X2Q, 16, 8, 1964},  {SW_LANE_I16X2Q, 32, 8, 3443},  {SW_LANE_I16X2Q, 32, 16, 4257},
-    {SW_LANE_I16X2Q, 32, 12, 4136}, {SW_LANE_I16X2Q, 32, 20, 4951}, {SW_LANE_I16X2Q, 32, 24, 4921},
-    {SW_LANE_I16X2Q, 32, 32, 4900},
-    {SW_LANE_I16X2Q, 64, 8, 3956},  {SW_LANE_I16X2Q, 64, 16, 4808}, {SW_LANE_I16X2Q, 64, 20, 5030},
-    {SW_LANE_I16X2Q, 64, 24, 5030}, {SW_LANE_I16X2Q, 64, 28, 4893}, {SW_LANE_I16X2Q, 64, 32, 5130}, {SW_LANE_I16X2, 32, 16, 3865},
-    {SW_LANE_I16X2, 32, 32, 4578},
+    {SW_LANE_I16X2Q, 16, 8, 2894},  {SW_LANE_I16X2Q, 32, 8, 4290},  {SW_LANE_I16X2Q, 32, 16, 4340},
+    {SW_LANE_I16X2Q, 32, 12, 4157}, {SW_LANE_I16X2Q, 32, 20, 4680}, {SW_LANE_I16X2Q, 32, 24, 5109},
+    {SW_LANE_I16X2Q, 32, 32, 5127}, {SW_LANE_I16X2Q, 32, 40, 5523}, {SW_LANE_I16X2Q, 64, 8, 4388},
+    {SW_LANE_I16X2Q, 64, 16, 4932}, {SW_LANE_I16X2Q, 64, 20, 5110}, {SW_LANE_I16X2Q, 64, 24, 5340},
+    {SW_LANE_I16X2Q, 64, 28, 5218}, {SW_LANE_I16X2Q, 64, 32, 5547}, {SW_LANE_I16X2Q, 64, 40, 5245},
+    {SW_LANE_I16X2, 32, 16, 3865},  {SW_LANE_I16X2, 32, 32, 4578},
 };
 constexpr double kChunkCost = 0.015;
 
@@ -1014,10 +1016,12 @@ int sw_probe_cell_rate_pass(int32_t lane_type, int32_t corrected, int32_t iters,
         return fail(SW_ERR_INVALID, "cells_per_second is NULL");
     if (lane_type < SW_LANE_I32 || lane_type > SW_LANE_I16X2Q)
         return fail(SW_ERR_INVALID, "lane_type must be I32, I16X2, I8X4 or I16X2Q");
-    if (corrected != 0 && corrected != 1)
-        return fail(SW_ERR_INVALID, "corrected must be 0 or 1");
+    if (corrected < 0 || corrected > 2)
+        return fail(SW_ERR_INVALID, "corrected must be 0, 1 or 2");
     if (corrected && lane_type == SW_LANE_I8X4)
-        return fail(SW_ERR_INVALID, "the s8x4 lanes have no shorter corrected pass");
+        return fail(SW_ERR_INVALID, "the s8x4 lanes have no corrected pass");
+    if (corrected == 2 && lane_type != SW_LANE_I16X2 && lane_type != SW_LANE_I16X2Q)
+        return fail(SW_ERR_INVALID, "the always-corrected pass runs on s16x2 lanes only");
     if (lane_type == SW_LANE_I16X2Q)
         lane_type = SW_LANE_I16X2;  // the same cell sequence on the same lane type
     if (iters < 1)
@@ -1028,7 +1032,8 @@ int sw_probe_cell_rate_pass(int32_t lane_type, int32_t corrected, int32_t iters,
     double cells = 0;
     float ms = 0;
     const int op = lane_type - 1;
-    int kr = swg::run_int_peak(op, corrected != 0, sms * 8, 256, iters, &cells, &ms, (cudaStream_t)cuda_stream);
+    int kr = swg::run_int_peak(op, corrected == 1, corrected == 2, sms * 8, 256, iters, &cells, &ms,
+                               (cudaStream_t)cuda_stream);
     if (kr)
         return cuda_fail(kr, "cell-rate probe");
     *cells_per_second = ms > 0 ? cells / (ms * 1e-3) : 0.0;

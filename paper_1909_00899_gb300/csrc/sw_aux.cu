@@ -260,10 +260,12 @@ int launch_pair_classes(const int64_t *q_off, int64_t n_pairs, const ClassTable 
 // exact instruction sequence of a scan-F pass (no loads, shuffles or scan),
 // so the measured rate is the ceiling of that sequence on this GPU.  CORR:
 // the shorter corrected pass (every substitution score >= -o), which raises
-// the diagonal and E by the decaying carry d; else the plain general pass.
+// the diagonal and E by the decaying carry d; AC: the always-corrected pass
+// of the long-query split kernels (the floor of H on the diagonal, h one DPX
+// add-max); else the plain general pass.
 // op 0: int32 cells, 1: s16x2, 2: s8x4 (plain only).
 // ---------------------------------------------------------------------------
-template <class LT, bool CORR = false>
+template <class LT, bool CORR = false, bool AC = false>
 __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uint32_t one, int *sink)
 {
     using T = typename LT::T;
@@ -284,9 +286,14 @@ __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uin
         T d = LT::d0_of(X[K / 2], k);  // a carry that changes every column
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const T h = LT::h_of(hd, (j & 1) ? P1 : P0, E[j], k);
+            const T h = AC ? LT::addmax(hd, (j & 1) ? P1 : P0, E[j]) : LT::h_of(hd, (j & 1) ? P1 : P0, E[j], k);
             const T ho = LT::ho_of(h, k);
-            if constexpr (CORR) {
+            if constexpr (AC) {
+                hd = LT::max3(X[j], d, k.xinit);
+                d = LT::dstep(d, k);
+                X[j] = LT::addmax(F, k.negO, ho);
+                E[j] = LT::max3(LT::fadd(E[j], k.negE32, k), d, X[j]);
+            } else if constexpr (CORR) {
                 hd = LT::xd_corr(X[j], d, k);
                 d = LT::dstep(d, k);
                 X[j] = LT::addmax(F, k.negO, ho);
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(256) cell_peak_kernel(int iters, int seed, uin
         sink[0] = acc;
 }
 
-int run_int_peak(int op, bool corrected, int blocks, int threads, int iters, double *cells, float *ms,
+int run_int_peak(int op, bool corrected, bool always, int blocks, int threads, int iters, double *cells, float *ms,
                  cudaStream_t st)
 {
     cudaEvent_t a, b;
@@ -327,7 +334,9 @@ int run_int_peak(int op, bool corrected, int blocks, int threads, int iters, dou
         return (int)err;
     const uint32_t one = 1;
     auto go = [&](void) {
-        if (op == 0 && corrected)
+        if (op == 1 && always)
+            cell_peak_kernel<LaneI16x2D, true, true><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
+        else if (op == 0 && corrected)
             cell_peak_kernel<LaneI32D, true><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);
         else if (op == 0)
             cell_peak_kernel<LaneI32><<<blocks, threads, 0, st>>>(iters, 12345, one, sink);

@@ -154,8 +154,10 @@ int api_check_align_args(const sw_profile *prof, const uint8_t *db, const int64_
 int api_launch_plan(const Plan &pl, bool lazy, const BatchArgs &a, int sms, cudaStream_t st);
 
 // Cell-rate probe of the plain pass for the roofline: 'op' selects the
-// lane type (0 int32, 1 s16x2, 2 s8x4); returns cells updated and ms.
-int run_int_peak(int op, bool corrected, int blocks, int threads, int iters, double *cells, float *ms,
+// lane type (0 int32, 1 s16x2, 2 s8x4); corrected: the shorter corrected
+// pass; always: the always-corrected pass (s16x2 only); returns cells
+// updated and ms.
+int run_int_peak(int op, bool corrected, bool always, int blocks, int threads, int iters, double *cells, float *ms,
                  cudaStream_t st);
 
 }  // namespace swg

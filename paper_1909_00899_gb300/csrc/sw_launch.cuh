@@ -6,19 +6,41 @@
 
 namespace swg {
 
+// The dynamic shared-memory limit is an attribute of a kernel on each
+// device: set it once per kernel and device (the current one).  Each
+// launcher instantiation owns its flags (every kernel here has the same
+// function type, so the flags cannot live in a helper keyed by that type).
+constexpr int kMaxDev = 64;
+struct SmemAttrOnce {
+    std::once_flag once[kMaxDev];
+    cudaError_t err[kMaxDev];
+};
+
+template <class Kern>
+int set_smem_attr_once(SmemAttrOnce &st, Kern kern, size_t bytes)
+{
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return (int)e;
+    if (dev < 0 || dev >= kMaxDev)
+        return (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    std::call_once(st.once[dev], [&] {
+        st.err[dev] = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    });
+    return (int)st.err[dev];
+}
+
 template <class LT, int L, int S, bool LAZY, bool ENDS = false, bool PIECES = false>
 int launch_batch_inst(const BatchArgs &a, int num_sms, cudaStream_t st)
 {
     auto kern = sw_batch_kernel<LT, L, S, LAZY, ENDS, PIECES>;
     // alphabet of at most 32 residues + the unknown and the inert rows
     constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-    });
-    if (attr_err != cudaSuccess)
-        return (int)attr_err;
+    static SmemAttrOnce attr;  // one per kernel instantiation
+    const int attr_err = set_smem_attr_once(attr, kern, kMaxSmem);
+    if (attr_err != (int)cudaSuccess)
+        return attr_err;
     const size_t smem = (size_t)(a.A + 2) * L * SegPad<S, LT::VEC>::value * sizeof(typename LT::Elem);
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem);

@@ -58,7 +58,7 @@ __host__ __device__ __forceinline__ int split_pb(int o)
     return D0 ? o : LaneQ16::PB;
 }
 
-template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false>
+template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false, bool AC = false>
 // len: this group's reference length; ncols: the warp's longest (every
 // lane runs ncols columns, columns past len use the inert row A+1).
 // LAZY: the lazy-F loop of Alg. 1 over the 2L virtual lanes instead of the
@@ -74,6 +74,17 @@ template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false>
 // the maximum holds exactly at the cells that reached it.  A half whose
 // maximum ends below the alignment's score may keep a stale note; it never
 // wins the final reduction.
+// AC (always corrected; scan-F scores with D0): every column runs the
+// corrected pass, with no warp vote on the carry (on protein data nearly
+// every column carries F across lanes), and the zero floor of H moves from h
+// to the diagonal.  h = max(Xd + P', E) is then one DPX add-max, and the
+// diagonal max(X, d_j, -o) one vimax3, where the plain corrected pass needs
+// an extra addition for the relu form.  Dropping the floor from h leaves
+// every value exact above its floor (H >= 0, and E, F, X >= -o in X-space):
+// a value under its floor only ever meets maxima with values that carry the
+// floor, and the one place where it could be raised again -- the diagonal,
+// where M is added -- takes the floor explicitly.  So h, the maximum and
+// everything above -o are unchanged.
 __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8_t *ref, int64_t start, int len,
                                                int ncols, int A, int o, int e, uint32_t one, bool has_prev,
                                                bool has_next, int2 *bnd, int gl,
@@ -81,6 +92,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                                                int *end_q = nullptr)
 {
     static_assert(!(LAZY && ENDS), "end cells: scan-F only");
+    static_assert(!AC || (D0 && !LAZY && !ENDS), "always-corrected pass: D0 scan-F scores only");
     using LT = LaneQ16;
     using T = uint32_t;
     constexpr int SP = SegPad<S, 4>::value;
@@ -170,7 +182,28 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 hd = fadd_u32(v, m16, lo_in);  // (lo_in, low half of v)
 
             T hpair = k.hzero;
-            if (!LAZY && __any_sync(FULL, LT::carry_pos(c_prev, k))) {
+            if constexpr (AC) {
+                T d = LT::d0_of(c_prev, k);
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    if (j % V == 0)
+                        LT::template load_vec<L, SP>(pbase, res, gl, j / V, Pv);
+                    // h = max(Xd + P', E) with the floor carried by the diagonal
+                    const T h = LT::addmax(hd, Pv[j % V], E[j]);
+                    hd = LT::max3(X[j], d, k.xinit);
+                    d = LT::dstep(d, k);
+                    const T ho = LT::ho_of(h, k);
+                    X[j] = LT::addmax(F, k.negO, ho);
+                    E[j] = LT::max3(LT::fadd(E[j], k.negE32, k), d, X[j]);
+                    F = LT::addmax(F, k.negE, ho);
+                    if (j & 1)
+                        mx = LT::max3(mx, hpair, h);
+                    else if (j == S - 1)
+                        mx = LT::max2(mx, h);
+                    else
+                        hpair = h;
+                }
+            } else if (!LAZY && __any_sync(FULL, LT::carry_pos(c_prev, k))) {
                 T d = LT::d0_of(c_prev, k);
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
@@ -353,7 +386,9 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                 if (gl == 0)
                     cin = fadd_u32(gb, m16, bf16);  // (boundary F or 0, low half of gb)
                 c_prev = cin;
-                hlast = LT::last_corr(X[S - 1], cin, k);
+                // AC: the diagonal handed to the next lane carries the floor
+                hlast = AC ? LT::max3(X[S - 1], LT::fadd(cin, k.negOS1_32, k), k.xinit)
+                           : LT::last_corr(X[S - 1], cin, k);
                 // the next chunk reads the high halves (this chunk's last position)
                 if (has_next && gl == L - 1 && rc < len)
                     reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, x);
@@ -396,17 +431,18 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
 // 128 registers a thread), the most each segment length fits without spills
 // (short segments serve short queries, which are latency-bound and want the
 // extra warps)
-template <int S, bool D0, bool ENDS = false>
+template <int S, bool D0, bool ENDS = false, bool AC = false>
 struct SplitMinBlocks {
-    static constexpr int value = D0 && !ENDS ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2)
+    static constexpr int value = AC        ? (S <= 20 ? 3 : 2)
+                                 : D0 && !ENDS ? (S <= 8 ? 5 : S <= 16 ? 4 : S <= 24 ? 3 : 2)
                                  : ENDS      ? (D0 ? (S <= 8 ? 4 : S <= 20 ? 3 : 2) : (S <= 8 ? 3 : 2))
                                              : (S <= 8 ? 4 : S <= 20 ? 3 : 2);
 };
 
 // PIECES: the launch splits long sequences into pieces (scores only, one
 // chunk); a separate instantiation so that the others stay as they are.
-template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false, bool PIECES = false>
-__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::value) sw_split_kernel(const BatchArgs p)
+template <int L, int S, bool D0, bool LAZY = false, bool ENDS = false, bool PIECES = false, bool AC = false>
+__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS, AC>::value) sw_split_kernel(const BatchArgs p)
 {
     constexpr int G = 32 / L;
     constexpr int SP = SegPad<S, 4>::value;
@@ -493,8 +529,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, ENDS>::va
                 p.r_end[seq[0]] = s > 0 ? re : -1;
             }
         } else {
-            const uint32_t mx = split_unit<L, S, D0, LAZY>(sprof, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
-                                                           has_prev, has_next, p.bnd, gl, &lazy_steps);
+            const uint32_t mx = split_unit<L, S, D0, LAZY, false, AC>(sprof, p.db, start, len, ncols, p.A, p.o, p.e,
+                                                                      p.one, has_prev, has_next, p.bnd, gl,
+                                                                      &lazy_steps);
             if (gl == 0) {
                 if constexpr (PIECES)
                     write_scores_pieces<LaneQ16>(mx, k, seq, p.flag_thresh, p.scores);

@@ -63,7 +63,9 @@ def test_invalid_arguments_rejected_without_cuda(swlib):
     assert L.sw_align_lazyf_batch(None, None, None, 0, 11, 1, None, None) == swlib.SW_ERR_INVALID
     assert L.sw_probe_cell_rate(7, 10, None, None) == swlib.SW_ERR_INVALID
     cps = ctypes.c_double(0.0)
-    assert L.sw_probe_cell_rate_pass(1, 2, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID
+    assert L.sw_probe_cell_rate_pass(1, 3, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID
+    assert L.sw_probe_cell_rate_pass(1, 2, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID  # int32: no AC pass
+    assert "s16x2" in swlib.sw_last_error()
     assert L.sw_probe_cell_rate_pass(3, 1, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID
     assert "s8x4" in swlib.sw_last_error()
 
@@ -84,9 +86,9 @@ def test_plan_query_covers_the_query_host_only(swlib):
                 assert m / (p["chunks"] * QC) > 0.5
     picks = {m: swlib.sw_plan_query(m) for m in (128, 512, 2048, 5000)}
     assert picks[128] == dict(lanes=16, seg_len=8, chunks=1, lane_type=4)
-    assert picks[512] == dict(lanes=32, seg_len=16, chunks=1, lane_type=4)
+    assert picks[512] == dict(lanes=64, seg_len=8, chunks=1, lane_type=4)
     assert picks[2048] == dict(lanes=64, seg_len=32, chunks=1, lane_type=4)
-    assert picks[5000] == dict(lanes=64, seg_len=20, chunks=4, lane_type=4)
+    assert picks[5000] == dict(lanes=32, seg_len=40, chunks=4, lane_type=4)
     # lengths between the benchmark's: the layout whose chunk the query fills
     # best at its measured rate (16 threads x 12/20/24/32, 32 threads x 28)
     mids = {300: (32, 12, 1), 600: (32, 20, 1), 700: (32, 24, 1), 1000: (32, 32, 1), 1700: (64, 28, 1),

@@ -19,8 +19,8 @@ ALL_PLANS = {
         (8, 32), (16, 32), (32, 32)],
     2: [(8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24), (32, 32)],
     3: [(8, 16), (16, 16), (32, 16)],
-    4: [(2, 16), (2, 32), (16, 8), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (64, 8), (64, 16),
-        (64, 20), (64, 24), (64, 28), (64, 32)],
+    4: [(2, 16), (2, 32), (16, 8), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (32, 40), (64, 8),
+        (64, 16), (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)],
 }
 
 

@@ -207,6 +207,45 @@ def test_both_corrected_passes(sw, kind):
                                                   % (o, e, mm, len(q)))
 
 
+AC_LAYOUTS = [(16, 8), (32, 8), (32, 16), (32, 24), (32, 32), (32, 40), (64, 8), (64, 16), (64, 24), (64, 28),
+              (64, 32), (64, 40)]
+
+
+@pytest.mark.parametrize("layout", AC_LAYOUTS)
+def test_always_corrected_pass(sw, layout):
+    """The split layouts that run the always-corrected pass (every column
+    corrected, the zero floor of H taken on the diagonal instead of h):
+    DNA scoring, where most h are below zero and the floor decides the
+    diagonal; mismatch scores at the pass's condition (-o, -o + 1); e = 0,
+    1 and o; one-chunk and multi-chunk queries, with query-side insertions
+    that carry F across many lanes and a copy of the query's middle planted
+    across chunk boundaries."""
+    L, S = layout
+    rng = np.random.default_rng(1012 + L * 100 + S)
+    QC = L * S
+    queries, refs = gap_adversary(rng, 4, 12, ylo=40, yhi=300)
+    q_long = synth.residues(rng, 3 * QC + 17, 4)
+    refs += [synth.residues(rng, int(n), 4) for n in (1, 2, 90, 1500)]
+    refs.append(np.concatenate([synth.residues(rng, 50, 4), q_long[QC - 40: 2 * QC + 40],
+                                synth.residues(rng, 30, 4)]))
+    db, off = pack_list(refs)
+    db_d, off_d = db_to_dev(db, off)
+    out = torch.empty(len(refs), dtype=torch.int32, device="cuda")
+    qs = queries[:3] + [synth.residues(rng, QC, 4), synth.residues(rng, QC + 1, 4), q_long]
+    # the last case (mismatch below -o) runs the general pass on the same layout
+    for o, e, mm in ((6, 1, -4), (5, 0, -5), (4, 4, -3), (3, 1, -3), (7, 2, -1), (3, 1, -4)):
+        M = synth.dna_matrix(match=2 if mm > -4 else 1, mismatch=mm)
+        for q in qs:
+            want = oracle.gotoh_batch(q, db, off, M, o, e)
+            prof = sw.Profile(q, M, sw.SW_LANE_I16X2Q, lanes=L, seg_len=S)
+            out.fill_(-7)
+            sw.sw_align_batch(prof, db_d, off_d, o, e, out)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy(), want, err_msg="L=%d S=%d o=%d e=%d mm=%d m=%d"
+                                          % (L, S, o, e, mm, len(q)))
+            prof.free()
+
+
 @pytest.mark.parametrize("kind", LANES)
 def test_unknown_database_residues(sw, kind):
     """Database codes >= A score the smallest matrix entry on every lane
@@ -336,6 +375,9 @@ def test_cell_rate_probe_runs(sw):
         plain = sw.sw_probe_cell_rate_pass(lane, 0, 1024)
         corr = sw.sw_probe_cell_rate_pass(lane, 1, 1024)
         assert 1e9 < corr < plain
+    # the always-corrected pass (s16x2 only) also does more than the plain one
+    ac = sw.sw_probe_cell_rate_pass(sw.SW_LANE_I16X2Q, 2, 1024)
+    assert 1e9 < ac < sw.sw_probe_cell_rate_pass(sw.SW_LANE_I16X2, 0, 1024)
 
 
 # ---------------------------------------------------------------------------
