@@ -10,9 +10,12 @@ comparison.  Metric: GCUPS = sum over alignments of m*n / seconds / 1e9.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One JSON line on rank 0.  Under torchrun every rank runs its own replica of
-the workload (the alignments are independent; no collective on the data
-path) and the time is the max over ranks.
+One JSON line on rank 0.  Under torchrun (N ranks) the database is N x
+100,000 sequences drawn the same way, sharded by length bin so that every
+rank holds 100,000 sequences with the same length profile (weak scaling);
+each rank aligns the queries against its own shard with no collective while
+aligning, the time is the max over ranks, and the score slices are gathered
+once after the timed region for the oracle spot check.
 """
 import argparse
 import json
@@ -52,13 +55,20 @@ def parse():
     ap.add_argument("--qlens", default=",".join(map(str, QLENS)),
                     help="comma-separated query lengths (profiling cases)")
     ap.add_argument("--quick", action="store_true",
-                    help="timed steps only: no oracle check, lazy-F, e2e, probe or CPU baseline")
+                    help="timed steps and the probe only: no oracle check, lazy-F, e2e, other workloads or "
+                         "CPU baseline")
     ap.add_argument("--workload", default="scale", choices=["scale", "pairs", "ragged", "serve", "width", "ends"],
                     help="scale: the default line; pairs/ragged/serve: the other workloads")
     ap.add_argument("--n-pairs", type=int, default=1_000_000)
     ap.add_argument("--n-queries", type=int, default=64, help="ragged: queries taken from the 10,000")
     ap.add_argument("--serve-db", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without the reads, ragged and serving sub-keys")
+    ap.add_argument("--extras-queries", type=int, default=256,
+                    help="ragged sub-key: queries taken from the 10,000")
+    ap.add_argument("--extras-requests", type=int, default=120,
+                    help="serving sub-key: requests per load")
     ap.add_argument("--streams", type=int, default=4,
                     help="CUDA streams the independent queries of a step are spread over")
     return ap.parse_args()
@@ -251,21 +261,36 @@ def main():
         args.no_cpu_baseline = True
         args.no_lazyf = True
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    torch.cuda.set_device(local)
+        if rank == 0:  # one build; the other ranks load what it made
+            libbuild.build()
+        torch.distributed.barrier()
     libbuild.build()
     lane = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32, "i16x2": sw.SW_LANE_I16X2,
             "i16x2q": sw.SW_LANE_I16X2Q, "i8x4": sw.SW_LANE_I8X4}[args.lane]
 
-    w = synth.workload_protein_scale(n_db=args.n_db, qlens=QLENS)
+    # the global database: n_db sequences per rank; each rank keeps its
+    # length-balanced shard (all of it on one GPU)
+    wg = synth.workload_protein_scale(n_db=args.n_db * world, qlens=QLENS)
+    shard_ids = None
+    w = wg
+    if world > 1:
+        shard_ids = dist.shard_by_length(wg["off"], world)[rank]
+        sdb, soff = dist.take(wg["db"], wg["off"], shard_ids)
+        w = dict(wg, db=sdb, off=soff)
     M, o, e = w["M"], w["o"], w["e"]
     workload = WORKLOAD if (QLENS, args.n_db) == ((128, 512, 2048, 5000), 100_000) else (
         "protein queries m in {%s} vs %d db seqs, log-normal lengths (median 300, sigma 0.76, "
         "clip [20,35000]), o=11 e=1" % (",".join(map(str, QLENS)), args.n_db))
+    if world > 1:
+        workload += (", %d ranks: a database of %d sequences sharded by length bin, %d per rank"
+                     % (world, args.n_db * world, args.n_db))
     n_db = len(w["off"]) - 1
     total_res = int(w["off"][-1])
-    cells_step = sum(QLENS) * total_res
+    cells_step = sum(QLENS) * total_res  # this rank's cells per step
+    cells_all = sum(QLENS) * int(wg["off"][-1])  # every rank's
     stream = torch.cuda.current_stream()
     db_d = torch.from_numpy(w["db"]).cuda()
     off_d = torch.from_numpy(w["off"]).cuda()
@@ -344,13 +369,14 @@ def main():
         return ms
 
     # correctness spot check against the oracle on a sample (not timed)
-    check = None if args.quick else sample_check(w, outs, step, rank)
+    check = None if args.quick else sample_check(wg, outs, step, rank, shard_ids)
 
     sampler = ClockSampler(local)
     sampler.start()
     total_ms = timed(args.steps)
     clocks = sampler.stop()
-    gcups = cells_step * args.steps * world / (total_ms * 1e-3) / 1e9
+    own_ms = sum(step_ms)  # this rank's own time (total_ms is the max over ranks)
+    gcups = cells_all * args.steps / (total_ms * 1e-3) / 1e9
     median_ms = float(np.median(step_ms))
     if world > 1:
         median_ms = dist.max_over_ranks(median_ms, device="cuda")
@@ -385,6 +411,14 @@ def main():
     # end to end through the public API: host (pinned) inputs copied in,
     # scores copied out, inside the timed region
     e2e = None if args.quick else run_e2e(w, lane, args, stream, cells_step)
+    if e2e is not None and world > 1:
+        # every rank copied and aligned its own shard: the job's time is the
+        # slowest rank's, its cells every rank's
+        e2e_ms = dist.max_over_ranks(e2e["ms"], device="cuda")
+        e2e["value"] = cells_all * e2e["steps"] / (e2e_ms * 1e-3) / 1e9
+        e2e["h2d_bytes_per_step"] = int(dist.sum_over_ranks(e2e["h2d_bytes_per_step"], device="cuda"))
+        e2e["d2h_bytes_per_step"] = int(dist.sum_over_ranks(e2e["d2h_bytes_per_step"], device="cuda"))
+        e2e["ms"] = e2e_ms
 
     # roofline of the dominant kernel: the longest query's call is its
     # chunk launches (plus a profile build, the length order, the overflow
@@ -451,18 +485,21 @@ def main():
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ms_per_step_median": median_ms,
-        "value_median_step": cells_step * world / (median_ms * 1e-3) / 1e9, "higher_is_better": True,
+        "value_median_step": cells_all / (median_ms * 1e-3) / 1e9, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "s16x2+int32" if cells_per_op == 2 else
         ("int32" if cells_per_op == 1 else "s8x4+int32"), "data": "synthetic",
         "config": {"workload": workload, "n_db": n_db, "db_residues": total_res,
                    "cells_per_step": cells_step, "lane": args.lane, "plan_longest": plan,
                    "l2": "flushed between timed steps (512 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": ("database sharded by length bin over %d ranks (no collective while "
+                                   "aligning; scores gathered once, untimed)" % world) if world > 1
+                                  else "single GPU",
+                   "db_residues_all_ranks": int(wg["off"][-1]), "cells_per_step_all_ranks": cells_all},
         "per_query_gcups": {str(m): m * total_res / (t * 1e-3) / 1e9 for m, t in zip(QLENS, per_q)},
         "plans": {str(m): p for m, p in zip(QLENS, plans)},
         "streams": args.streams,
         "lazyf": lazy,
-        "scan_vs_lazyf": (gcups / world / lazy["value"]) if lazy else None,
+        "scan_vs_lazyf": (cells_step * args.steps / (own_ms * 1e-3) / 1e9 / lazy["value"]) if lazy else None,
         "scan_int32": scan_i32,
         "scan_vs_lazyf_per_query": ({str(m): (m * total_res / (t * 1e-3) / 1e9) / lazy["per_query_gcups"][str(m)]
                                      for m, t in zip(QLENS, per_q)} if lazy else None),
@@ -498,33 +535,55 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(w, QLENS, args.cpu_seconds)
+    if world == 1 and not args.quick and not args.no_extras:
+        # the other workloads, each with its own clock record and an oracle
+        # spot check: reads vs windows with the lazy-F worst case, the
+        # ragged batch, serving
+        del outs, db_d, off_d, flush
+        torch.cuda.empty_cache()
+        pl = pairs_summary(args, cpu=False)
+        line["gap_adversary"] = pl.pop("gap_adversary")
+        line["pairs"] = pl
+        torch.cuda.empty_cache()
+        line["ragged"] = ragged_summary(args, args.extras_queries)
+        torch.cuda.empty_cache()
+        line["serving"] = serving_summary(args, args.extras_requests)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def sample_check(w, outs, step, rank):
-    """Scores of a sample of sequences, per query, against the oracle."""
+def sample_check(w, outs, step, rank, shard_ids=None):
+    """Scores of a sample of sequences, per query, against the oracle.  w is
+    the global database; with shards, every rank's score slices are first
+    gathered into its order (the one collective of the data path)."""
     import numpy as np
     import torch
 
     import oracle
+    from paper_1909_00899_gb300 import dist
     profs = step()
     torch.cuda.synchronize()
     del profs
     n = len(w["off"]) - 1
+    if shard_ids is not None:
+        full = dist.gather_scores(torch.stack(outs), shard_ids, n).cpu().numpy()
+    else:
+        full = torch.stack(outs).cpu().numpy()
+    if rank != 0:
+        return None
     rng = np.random.default_rng(7)
     ids = np.sort(rng.choice(n, size=min(n, 64), replace=False))
     sub_db, sub_off = _subset(w["db"], w["off"], ids)
     bad = 0
-    for q, out in zip(w["queries"], outs):
+    for k, q in enumerate(w["queries"]):
         want = oracle.gotoh_batch(q, sub_db, sub_off, w["M"], w["o"], w["e"])
-        got = out.cpu().numpy()[ids]
-        bad += int((got != want).sum())
+        bad += int((full[k][ids] != want).sum())
     if bad:
         raise SystemExit("bench: %d sampled scores differ from the oracle" % bad)
-    return {"sampled": int(len(ids)) * len(w["queries"]), "mismatches": 0}
+    return {"sampled": int(len(ids)) * len(w["queries"]), "mismatches": 0,
+            "gathered_from_ranks": 1 if shard_ids is None else int(torch.distributed.get_world_size())}
 
 
 def run_e2e(w, lane, args, stream, cells_step):
@@ -578,7 +637,7 @@ def run_e2e(w, lane, args, stream, cells_step):
     ms = a.elapsed_time(b)
     h2d = db_h.numel() + off_h.numel() * 8 + sum(len(q) for q in w["queries"]) + 400 * 2 * len(QLENS)
     d2h = 4 * n_db * len(QLENS)
-    return {"value": cells_step * steps / (ms * 1e-3) / 1e9, "unit": "GCUPS",
+    return {"value": cells_step * steps / (ms * 1e-3) / 1e9, "unit": "GCUPS", "ms": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
 
 
@@ -600,14 +659,25 @@ def _events_ms(fn, stream, reps=1):
 
 
 def run_pairs(args):
-    """DNA reads against their own 2 kbp reference windows (1M pairs)."""
+    """DNA reads against their own 2 kbp reference windows (1M pairs): one
+    JSON line."""
+    print(json.dumps(pairs_summary(args, cpu=not args.no_cpu_baseline)), flush=True)
+
+
+def pairs_summary(args, cpu=True):
+    """DNA reads against their own 2 kbp reference windows (1M pairs): scan-F
+    on every lane type, end cells, lazy-F and its corrective factor per read
+    class, and the synthetic lazy-F worst case (query X+Y+Z vs reference
+    X+Z); sampled scores checked against the oracle.  The clocks are sampled
+    over the whole GPU part."""
     import numpy as np
     import torch
 
     import oracle
     from paper_1909_00899_gb300 import sw, synth
-    torch.cuda.set_device(0)
     w = synth.workload_reads(n_pairs=args.n_pairs)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     n = len(w["q_off"]) - 1
     qlen = np.diff(w["q_off"])
     rlen = np.diff(w["r_off"])
@@ -742,6 +812,7 @@ def run_pairs(args):
     want = oracle.gotoh_pairs(sb["q"], sb["q_off"], sb["r"], sb["r_off"], w["M"], w["o"], w["e"])
     if not np.array_equal(got[sample], want):
         raise SystemExit("pairs: sampled scores differ from the oracle")
+    clocks = sampler.stop()
     best = max(res.values(), key=lambda r: r["gcups"])
     line = {"metric": "GCUPS reads vs windows (scan-F, bit-exact)", "value": best["gcups"], "unit": "GCUPS",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -752,8 +823,9 @@ def run_pairs(args):
             "lazyf_by_lane": {"int32": lazy_int32, "s16x2_split": lazy_split},
             "scan_vs_lazyf": lazy["ms"] / best["ms"],
             "per_class": per_class, "largest_margin_class": worst,
+            "gap_adversary": per_class["gap_adversary"], "clocks": clocks,
             "check": {"sampled": int(sample.size), "mismatches": 0}}
-    if not args.no_cpu_baseline:
+    if cpu:
         # about cpu_seconds of work at ~10 GCUPS on the host cores
         ids = np.arange(0, n, max(1, int(cells / (args.cpu_seconds * 1e10))))
         sb = _pairs_subset(w, ids)
@@ -763,7 +835,7 @@ def run_pairs(args):
         c = float((np.diff(sb["q_off"]) * np.diff(sb["r_off"])).sum())
         line["cpu_baseline"] = {"value": c / dt / 1e9, "unit": "GCUPS", "cores": len(os.sched_getaffinity(0)),
                                 "kind": "oracle", "sample": "%d of %d pairs (%.3g cells, %.1f s)" % (len(ids), n, c, dt)}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_width(args):
@@ -875,6 +947,10 @@ def _pairs_subset(w, ids):
 
 
 def run_ragged(args):
+    print(json.dumps(ragged_summary(args, args.n_queries)), flush=True)
+
+
+def ragged_summary(args, n_queries):
     """Ragged batch: a deterministic, length-stratified subset of 10,000
     protein queries (log-uniform 32..4096) against 200k log-normal sequences,
     every query's alignment captured in one CUDA graph with the autotuned
@@ -885,25 +961,29 @@ def run_ragged(args):
     import oracle
     from paper_1909_00899_gb300 import autotune, sw, synth
     from paper_1909_00899_gb300.batch import BatchAligner
-    torch.cuda.set_device(0)
     rng = synth.rng_for(3)
     M = synth.protein_matrix(rng)
     qlens_all = synth.lengths_loguniform(rng, 10_000, 32, 4096)
     db, off = synth.random_db(rng, 200_000, 20, "lognormal", median=300, sigma=0.76, lo=20, hi=35000)
     order = np.argsort(qlens_all, kind="stable")
-    pick = order[np.linspace(0, len(order) - 1, args.n_queries).astype(int)]
+    pick = order[np.linspace(0, len(order) - 1, n_queries).astype(int)]
     queries = [synth.residues(np.random.default_rng([5, int(i)]), int(qlens_all[i]), 20) for i in pick]
     db_d = torch.from_numpy(db).cuda()
     off_d = torch.from_numpy(off).cuda()
     h = sw.Database(db_d, off_d)
-    # autotune against the database itself (one query per length bin)
-    table = autotune.tune(h, M, 11, 1, lengths=[48, 100, 200, 400, 800, 1600, 3200], reps=1)
+    # autotune against the database itself (one query per length bin), over
+    # the split layouts the batched launch runs
+    table = autotune.tune(h, M, 11, 1, lengths=[48, 100, 200, 400, 800, 1600, 3200], reps=1,
+                          lanes=(sw.SW_LANE_I16X2Q,))
     out = torch.empty((len(queries), h.n), dtype=torch.int32, device="cuda")
     ba = BatchAligner(h, M, 11, 1, table=table, streams=args.streams).prepare(queries, out)
     st = ba.stream
+    layouts = ba.layouts()
     for _ in range(args.warmup):
         ba.run()
     ms = []
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     for _ in range(args.steps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -912,6 +992,7 @@ def run_ragged(args):
         b.record(st)
         b.synchronize()
         ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
     total_res = int(off[-1])
     cells = float(sum(len(q) for q in queries)) * total_res
     got = out.cpu().numpy()
@@ -921,6 +1002,12 @@ def run_ragged(args):
         want = oracle.gotoh_batch(queries[k], sdb, soff, M, 11, 1)
         if not np.array_equal(got[k][ids], want):
             raise SystemExit("ragged: sampled scores differ from the oracle")
+    # launches of one replay: one per layout and, when some pairs could pass
+    # the packed lanes' range, one int32 launch per int32 layout
+    thresh = 32767 - (4096 + 128 - 11) - int(M.max())
+    skip_len = -(-thresh // int(M.max()))
+    n_i32 = len({(32, 8) if m <= 256 else (32, 16) if m <= 512 else (32, 32) for m in map(len, queries)
+                 if m >= skip_len}) if int(np.diff(off).max()) >= skip_len else 0
     line = {"metric": "GCUPS ragged batch (graph replay, bit-exact)", "value": cells / (np.mean(ms) * 1e-3) / 1e9,
             "unit": "GCUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "data": "synthetic",
@@ -929,11 +1016,20 @@ def run_ragged(args):
                        "cells_per_step": cells, "full_config_cells": float(qlens_all.sum()) * total_res},
             "ms_per_step": float(np.mean(ms)),
             "projected_full_config_s": float(qlens_all.sum()) * total_res / (cells / (np.mean(ms) * 1e-3)),
-            "autotune": table.to_json(), "check": {"queries_checked": 8, "db_sample": 300}}
-    print(json.dumps(line), flush=True)
+            "autotune": table.to_json(), "clocks": clocks, "check": {"queries_checked": 8, "db_sample": 300},
+            "mode": "batched" if ba.multi is not None else "per_query",
+            "launches_per_replay": (len(layouts) + n_i32) if ba.multi is not None else None,
+            "launch_bins": [{"lanes": x[0], "seg_len": x[1], "kernel": "phase" if x[2] else "fused-chunk"}
+                            for x in layouts]}
+    ba.free()
+    return line
 
 
 def run_serve(args):
+    print(json.dumps(serving_summary(args, args.serve_requests)), flush=True)
+
+
+def serving_summary(args, n_requests):
     """Serving: Poisson stream of protein queries (log-uniform 50..10,000)
     against a resident database of 1M log-normal sequences (~350M residues),
     admitted by a memory budget; p50/p99 latency at 50% and 90% of the
@@ -943,7 +1039,6 @@ def run_serve(args):
 
     import oracle
     from paper_1909_00899_gb300 import serve, sw, synth
-    torch.cuda.set_device(0)
     rng = synth.rng_for(4)
     M = synth.protein_matrix(rng)
     db, off = synth.random_db(rng, args.serve_db, 20, "lognormal", median=300, sigma=0.555, lo=20, hi=35000)
@@ -960,14 +1055,16 @@ def run_serve(args):
     budget = 48 << 30
     srv = serve.Server(h, M, 11, 1, slots=4, mem_budget=budget)
     srv.run(queries(4, 0))  # warm-up
-    qs = queries(args.serve_requests, 1)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    qs = queries(n_requests, 1)
     t0 = time.perf_counter()
     reqs = srv.run(qs)
     peak_qps = len(qs) / (time.perf_counter() - t0)
     peak_gcups = sum(len(q) for q in qs) * total_res / srv.wall / 1e9
     loads = {}
     for frac in (0.5, 0.9):
-        qs2 = queries(args.serve_requests, int(frac * 10))
+        qs2 = queries(n_requests, int(frac * 10))
         arr = serve.poisson_arrivals(np.random.default_rng([7, int(frac * 10)]), len(qs2), frac * peak_qps)
         srv2 = serve.Server(h, M, 11, 1, slots=4, mem_budget=budget)
         r2 = srv2.run(qs2, arr)
@@ -982,15 +1079,16 @@ def run_serve(args):
                 want = oracle.gotoh_batch(qs2[k], sdb, soff, M, 11, 1)
                 if not np.array_equal(r2[k].scores[ids], want):
                     raise SystemExit("serve: sampled scores differ from the oracle")
+    clocks = sampler.stop()
     line = {"metric": "serving latency p50/p99 and throughput (bit-exact)", "value": peak_gcups, "unit": "GCUPS",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "protein queries log-uniform 50..10000 vs %d resident log-normal sequences "
                                    "(median 300, sigma 0.555, %d residues), o=11 e=1, 4 slots, %d GB budget"
                                    % (h.n, total_res, budget >> 30),
-                       "requests_per_load": args.serve_requests},
-            "peak_qps": peak_qps, "loads": loads,
+                       "requests_per_load": n_requests},
+            "peak_qps": peak_qps, "loads": loads, "clocks": clocks,
             "check": {"requests_checked": "5%", "db_sample": 200}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 if __name__ == "__main__":

@@ -298,6 +298,51 @@ int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
                             unsigned long long *lazy_steps, void *cuda_stream);
 
 /*
+ * sw_multi — many profiled queries against one resident database in one
+ * persistent launch per layout (the ragged batch; every (query, sequence)
+ * alignment is independent, Sec. III).  sw_multi_create groups the queries
+ * by their layout, reads the database's offsets back once to order its
+ * sequences exactly by length, uploads the tables and that order and sizes
+ * the per-group boundary slots (it synchronises cuda_stream and allocates
+ * about 4 bytes per sequence plus the slots); sw_align_multi then issues a
+ * memset and one launch per layout (two when a layout holds both one- and
+ * several-chunk queries), plus one int32 launch per int32 layout when some
+ * pairs could overflow the packed lanes, with no host
+ * synchronisation: it can be captured into a CUDA graph.
+ *  - Queries of one chunk (per layout, one launch): every CTA walks the
+ *    queries in order, stages each one's profile once and pulls its
+ *    sequences, longest first, from the query's own counter, as the
+ *    per-query kernel does.
+ *  - Queries of several chunks (per layout, one launch): work units are
+ *    (query, tile of consecutive sequences of the length order),
+ *    tile-major so that the longest tiles of every query go first;
+ *    items_per_group (1..64, 0: the library's default, 4) sets the tile:
+ *    each lane group of a CTA takes that many sequences per unit; a unit
+ *    runs all chunks of its query inside one CTA, with each lane group's
+ *    chunk boundary row in its own slot of max_len columns (no
+ *    residue-sized rows per query).
+ *  - Packed lanes cannot overflow there: pairs with
+ *    min(m, n) * max(M) >= the s16x2 rescore threshold go to int32 lanes.
+ *  - profiles: host array of n_queries profiles, all built with the same
+ *    substitution matrix on SW_LANE_I16X2Q (or SW_LANE_AUTO, which chooses
+ *    it) with layouts of 16 or more virtual lanes; they and the database
+ *    handle must outlive the batch handle (SW_ERR_INVALID otherwise).
+ *  - scores_out: device int32, row-major [n_queries][row_stride],
+ *    row_stride >= the database's sequence count; row q holds query q's
+ *    scores in the database's order.
+ *  - gap_open <= 127 and the packed lanes' range check of sw_align_batch
+ *    (SW_ERR_RANGE otherwise: align such queries one by one).
+ *  - Calls on one handle share its counters and slots: do not overlap them.
+ */
+typedef struct sw_multi sw_multi; /* opaque, owned by the library */
+int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries,
+                    const sw_db *db, int32_t items_per_group,
+                    void *cuda_stream, sw_multi **out);
+int sw_align_multi(const sw_multi *batch, int32_t gap_open, int32_t gap_extend,
+                   int32_t *scores_out, int64_t row_stride, void *cuda_stream);
+int sw_multi_free(sw_multi *batch);
+
+/*
  * sw_align_batch_noalloc — sw_align_batch (same arguments, results and
  * errors) for callers that cannot let a library allocate device memory, for
  * example an application whose own allocator has reserved the device's
@@ -369,6 +414,15 @@ int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_secon
  */
 int sw_probe_cell_rate_pass(int32_t lane_type, int32_t corrected, int32_t iters,
                             double *cells_per_second, void *cuda_stream);
+
+/*
+ * sw_mem_available — device memory a new call could use now on the current
+ * device: the free memory (cudaMemGetInfo) plus the blocks the device's
+ * default stream-ordered pool holds unused (the library's scratch and
+ * profiles come from that pool, which keeps freed blocks).  Host query, no
+ * stream work; the serving loop admits requests against it.
+ */
+int sw_mem_available(int64_t *bytes);
 
 /* Library version, e.g. "0.1.0". */
 const char *sw_version(void);

@@ -1,10 +1,14 @@
 """Many queries against one resident database (ragged batches).
 
-Queries are binned by length; each bin's profiles are built with the layout
-the autotuner picked for it (or the built-in one), and the whole set of
-sw_align_db calls -- every query, every chunk launch, the overflow flagging
-and the int32 rescore -- is captured once into a CUDA graph and replayed.
-Scores land in a [n_queries, n_db] int32 device matrix.
+Each query's profile is built with the layout the autotuner picked for its
+length (or the built-in automatic one).  When every profile runs on the
+split s16x2 lanes (the automatic lane type), the whole batch is one
+sw_align_multi call -- one persistent launch per layout over every
+(query, tile of database sequences) unit, plus one int32 launch for the
+few pairs that could overflow the packed lanes -- captured once into a
+CUDA graph and replayed.  Otherwise every query's sw_align_db call is
+captured instead, spread over side streams.  Scores land in a
+[n_queries, n_db] int32 device matrix.
 """
 import numpy as np
 
@@ -12,11 +16,15 @@ from . import autotune, sw
 
 
 class BatchAligner:
-    """streams: the queries are spread round-robin over this many streams
-    that fork from and join back into the aligner's stream (inside the
-    graph too), so one query's launch tail overlaps the next query's work."""
+    """mode: "multi" (one batched launch per layout; the default), or
+    "per_query" (one sw_align_db per query, spread round-robin over
+    `streams` side streams that fork from and join back into the aligner's
+    stream).  "multi" falls back to "per_query" when a profile cannot join
+    the batched launch (another lane type, or gap costs beyond its packed
+    lanes)."""
 
-    def __init__(self, db, M, o, e, lane=sw.SW_LANE_AUTO, table=None, stream=None, streams=4):
+    def __init__(self, db, M, o, e, lane=sw.SW_LANE_AUTO, table=None, stream=None, streams=4, mode="multi",
+                 items_per_group=0):
         import torch
         self.db = db
         self.M = np.ascontiguousarray(M, dtype=np.int8)
@@ -25,15 +33,19 @@ class BatchAligner:
         self.table = table
         self.stream = stream or torch.cuda.Stream()
         self.side = [torch.cuda.Stream() for _ in range(max(1, streams))]
+        self.mode = mode
+        self.items_per_group = int(items_per_group)  # batched tile: sequences per lane group (0: default)
         self.graph = None
         self.profiles = []
         self.order = None
+        self.multi = None
 
     def _profile(self, q):
         plan = self.table.plan(len(q)) if self.table is not None else None
         if plan is not None:
             lane, L, S = plan
-            return sw.Profile(q, self.M, lane, stream=self.stream, lanes=L, seg_len=S)
+            if not (self.mode == "multi" and lane == sw.SW_LANE_I16X2Q and L < 16):
+                return sw.Profile(q, self.M, lane, stream=self.stream, lanes=L, seg_len=S)
         return sw.Profile(q, self.M, self.lane, stream=self.stream)
 
     def prepare(self, queries, out):
@@ -49,9 +61,22 @@ class BatchAligner:
             self.profiles[i] = self._profile(queries[i])
         self.stream.synchronize()  # profiles are built on self.stream
         self.out = out
-        with torch.cuda.stream(self.stream):
-            # one eager pass: sets kernel attributes and warms the memory pool
-            self._enqueue()
+        # one eager pass: sets kernel attributes, warms the memory pool and
+        # (batched) checks the gap costs against the packed lanes
+        if self.mode == "multi":
+            try:
+                self.multi = sw.Multi(self.profiles, self.db, stream=self.stream,
+                                      items_per_group=self.items_per_group)
+                with torch.cuda.stream(self.stream):
+                    self._enqueue()
+            except sw.SwError:
+                if self.multi is not None:
+                    self.multi.free()
+                self.multi = None
+                self.mode = "per_query"
+        if self.multi is None:
+            with torch.cuda.stream(self.stream):
+                self._enqueue()
         self.stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=self.stream, capture_error_mode="thread_local"):
@@ -61,6 +86,9 @@ class BatchAligner:
 
     def _enqueue(self):
         import torch
+        if self.multi is not None:
+            sw.sw_align_multi(self.multi, self.o, self.e, self.out, stream=self.stream)
+            return
         fork = torch.cuda.Event()
         fork.record(self.stream)
         for st in self.side:
@@ -72,6 +100,13 @@ class BatchAligner:
             j = torch.cuda.Event()
             j.record(st)
             self.stream.wait_event(j)
+
+    def layouts(self):
+        """The launch bins of the batched mode: distinct (virtual lanes,
+        segment length, one chunk or several) of the batch's profiles; a
+        replay issues one launch per bin plus at most three int32 launches."""
+        return sorted({(p.plan()["lanes"], p.plan()["seg_len"], p.plan()["chunks"] == 1)
+                       for p in self.profiles if p.qlen > 0})
 
     def run(self):
         """Replays the captured graph on the aligner's stream."""
@@ -87,6 +122,9 @@ class BatchAligner:
         return self.out
 
     def free(self):
+        if self.multi is not None:
+            self.multi.free()
+            self.multi = None
         for p in self.profiles:
             if p is not None:
                 p.free()

@@ -31,15 +31,6 @@ int launch_batch_q16_pieces(const Plan &pl, bool lazy, const BatchArgs &a, int n
 
 using swg::Plan;
 
-struct sw_db {
-    int device = 0;
-    const uint8_t *res = nullptr;
-    const int64_t *off = nullptr;
-    int64_t n = 0;
-    int64_t total = 0;
-    int32_t *order = nullptr;  // length-binned order, longest first (owned)
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -1002,6 +993,29 @@ int sw_stream_sync(void *cuda_stream, int64_t timeout_ms)
             return fail(SW_ERR_TIMEOUT, "stream still busy after %lld ms", (long long)timeout_ms);
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
+}
+
+int sw_mem_available(int64_t *bytes)
+{
+    if (!bytes)
+        return fail(SW_ERR_INVALID, "bytes is NULL");
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    size_t free_b = 0, total_b = 0;
+    if (err == cudaSuccess)
+        err = cudaMemGetInfo(&free_b, &total_b);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "cudaMemGetInfo");
+    // the library's scratch comes from the device's default stream-ordered
+    // pool, which keeps freed blocks: those are available to the next call
+    uint64_t reserved = 0, used = 0;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    }
+    *bytes = (int64_t)free_b + (int64_t)(reserved > used ? reserved - used : 0);
+    return SW_OK;
 }
 
 int sw_probe_cell_rate(int32_t lane_type, int32_t iters, double *cells_per_second, void *cuda_stream)

@@ -67,8 +67,11 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
                                                         const int64_t *start, const int *len, int ncols, int A,
                                                         int o, int e, uint32_t one, bool has_prev, bool has_next,
                                                         int2 *bnd, int gl, unsigned long long &lazy_steps,
-                                                        int *end_r = nullptr, int *end_q = nullptr)
+                                                        int *end_r = nullptr, int *end_q = nullptr,
+                                                        const int64_t *bstart = nullptr)
 {
+    // boundary rows are indexed from bstart[c] (default: the residues' start)
+    const int64_t *bs = bstart ? bstart : start;
     using T = typename LT::T;
     constexpr int CELLS = LT::CELLS;
     constexpr int SP = SegPad<S, LT::VEC>::value;
@@ -105,7 +108,7 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
             myres[c] = r < len[c] ? min((int)ref[start[c] + r], A) : A + 1;
             mybnd[c] = make_int2(-o, 0);
             if (has_prev && r < len[c])
-                mybnd[c] = bnd[start[c] + r];
+                mybnd[c] = bnd[bs[c] + r];
         }
         const int cols = min(L, ncols - r0);
         for (int rr = 0; rr < cols; ++rr) {
@@ -223,7 +226,7 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
 #pragma unroll
                     for (int c = 0; c < CELLS; ++c)
                         if (r < len[c])
-                            bnd[start[c] + r] = make_int2(LT::x_true(hlast, c), LT::x_true(x, c));
+                            bnd[bs[c] + r] = make_int2(LT::x_true(hlast, c), LT::x_true(x, c));
                 }
             } else {
 #pragma unroll
@@ -275,7 +278,7 @@ __device__ __forceinline__ typename LT::T striped_unit(const typename LT::Elem *
 #pragma unroll
                     for (int c = 0; c < CELLS; ++c)
                         if (r < len[c])
-                            bnd[start[c] + r] = make_int2(LT::x_true(hlast, c), LT::x_true(fb, c));
+                            bnd[bs[c] + r] = make_int2(LT::x_true(hlast, c), LT::x_true(fb, c));
                 }
             }
         }

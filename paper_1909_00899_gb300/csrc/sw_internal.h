@@ -141,6 +141,16 @@ struct sw_profile {
     int32_t maxM = 0, minM = 0;
 };
 
+// A device-resident database handle (opaque in the public header).
+struct sw_db {
+    int device = 0;
+    const uint8_t *res = nullptr;
+    const int64_t *off = nullptr;
+    int64_t n = 0;
+    int64_t total = 0;
+    int32_t *order = nullptr;  // length-binned order, longest first (owned)
+};
+
 namespace swg {
 
 // Host helpers of sw_api.cu shared with other host translation units.
@@ -159,5 +169,52 @@ int api_launch_plan(const Plan &pl, bool lazy, const BatchArgs &a, int sms, cuda
 // updated and ms.
 int run_int_peak(int op, bool corrected, bool always, int blocks, int threads, int iters, double *cells, float *ms,
                  cudaStream_t st);
+
+}  // namespace swg
+
+namespace swg {
+
+// One query of a batched multi-query launch (device table entry).
+struct MultiQuery {
+    const int8_t *prof;    // raw profile of its layout: [C][A][L*S] int8
+    int32_t qlen;
+    int32_t C;             // chunks of its layout
+    int64_t row;           // its score row (the query's index in the batch)
+};
+
+// Parameters of one multi-query launch: every (query, tile) unit of
+// queries[0 .. n_queries) x the first n_items entries of the length order.
+struct MultiArgs {
+    const MultiQuery *queries;
+    int32_t n_queries;
+    int32_t A, o, e, min_m;
+    uint32_t one;
+    const uint8_t *db;
+    const int64_t *off;
+    const int32_t *order;   // sequence ids by length, longest first
+    int64_t n_items;        // entries of order covered
+    int32_t skip_len;       // pairs with min(query length, sequence length) >= skip_len:
+                            // skipped by the packed launch, the only ones of the int32 launch
+    int32_t *scores;        // row-major [query][row_stride]
+    int64_t row_stride;
+    int32_t k_items;        // sequences per lane group per unit (the tile is k_items x groups per CTA)
+    unsigned long long *counter;  // unit counter (phase kernel: one per query), zero at launch
+    uint32_t *bnd;          // per-group boundary-row slots (32-bit words), null when C == 1 throughout
+    int64_t bnd_stride;     // words per group slot
+};
+
+// multi-query launchers (sw_k_multi*.cu): split s16x2 layouts (virtual lanes
+// x segment length; phase: the phase kernel of single-chunk queries, whose
+// counter is one per query, else the fused-chunk kernel) and the int32
+// layouts 32 x {8, 16, 32} of the pairs that could overflow the packed
+// lanes; grid is fixed by the caller (its boundary slots are sized for it).
+int launch_multi_split(int VL, int S, bool phase, const MultiArgs &a, int grid, cudaStream_t st);
+int launch_multi_i32(int S, const MultiArgs &a, int grid, cudaStream_t st);
+// CTAs per SM the launch runs with (0 for a layout without a kernel)
+int multi_split_blocks_per_sm(int VL, int S, bool phase, bool d0, int A);
+int multi_i32_blocks_per_sm(int S, bool d0, int A);
+// groups (one item each) per CTA of a layout of `lanes` virtual lanes (the
+// int32 kernels' 32 lanes per alignment count as 64: one group per warp)
+int multi_groups_per_cta(int lanes);
 
 }  // namespace swg

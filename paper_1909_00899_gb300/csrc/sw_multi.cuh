@@ -1,0 +1,275 @@
+// Many independent queries against one resident database in one persistent
+// launch per layout (the ragged batch; the paper's independent alignments,
+// Sec. III, across queries as well as database sequences).
+//
+// Work unit: (query q, tile t), where a tile is K * GPC consecutive entries
+// (K = k_items)
+// of the database's order, exactly by length (longest first), and GPC is the
+// number of lane groups of a CTA: every group takes K sequences of the tile,
+// the k-th ones of all groups adjacent in the order, so the groups of a CTA
+// finish each step together.  A single-chunk query stages its profile once
+// per unit for all K steps.
+// Units are numbered tile-major (unit = t * n_queries + q): the longest
+// tiles of every query go first, which keeps the launch's tail short without
+// splitting long sequences.  Persistent CTAs pull units from one counter.
+//
+// A unit runs every chunk of its query in order inside the CTA: the CTA
+// stages chunk c's profile into shared memory, every group aligns its
+// sequence against it (Alg. 6 per column, as in the per-query kernels), and
+// the chunk boundary row -- the corrected H - o and the F leaving the chunk,
+// per reference column, 8 bytes -- goes to the group's own slot of max_len
+// columns in global memory (a few KB per group in practice, so it stays in
+// L2) instead of a row of every database residue per query.  The score is
+// the maximum over the chunks.
+//
+// That is the fused-chunk kernel, for queries of more than one chunk.
+// Single-chunk queries run the phase kernel below instead, whose inner loop
+// is the per-query kernel's (measured 5-20 % faster than the fused-chunk
+// structure on those layouts).
+//
+// Packed lanes never overflow here: an alignment of m x n cells scores at
+// most max(M) * min(m, n), so pairs with min(m, n) >= skip_len (the packed
+// lane's rescore threshold over max(M)) are left to a second launch on int32
+// lanes, which takes only those pairs.  They are the longest database
+// sequences against the longest queries, a prefix of the length order.
+#pragma once
+#include "sw_split.cuh"
+
+namespace swg {
+
+constexpr unsigned MULTI_FULL = 0xffffffffu;
+
+// The unit counter is fetched by one thread and broadcast through shared
+// memory; every thread reads it before the chunk-0 staging barrier, so the
+// next fetch (after the loop's top barrier) cannot overwrite an unread value.
+template <int L, int S, bool D0, bool AC>
+__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC>::value)
+    sw_multi_split_kernel(const MultiArgs p)
+{
+    constexpr int G = 32 / L;
+    constexpr int GPC = (BATCH_THREADS / 32) * G;
+    constexpr int SP = SegPad<S, 4>::value;
+    constexpr int QH = L * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sprof = reinterpret_cast<uint32_t *>(smem_raw);
+    __shared__ unsigned long long s_unit;
+
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = (int)(threadIdx.x >> 5) * G + lane / L;
+    const int K = p.k_items;
+    const int64_t per_tile = (int64_t)GPC * K;
+    const int64_t n_tiles = (p.n_items + per_tile - 1) / per_tile;
+    const int64_t n_units = n_tiles * p.n_queries;
+    const int pb = split_pb<D0>(p.o);
+    const LaneQ16::K k = LaneQ16::consts_pb(p.o, p.e, S, p.one, pb);
+    int2 *bnd = p.bnd ? reinterpret_cast<int2 *>(p.bnd + ((int64_t)blockIdx.x * GPC + grp) * p.bnd_stride) : nullptr;
+    const int total = (p.A + 2) * L * SP;
+
+    // stage chunk c of query Q: virtual lanes l and L + l paired in one
+    // word; row A: an unknown residue (the smallest entry), row A+1: inert
+    auto stage = [&](const MultiQuery &Q, int c) {
+        const int8_t *gprof = Q.prof + (size_t)c * p.A * 2 * QH;
+        const int qbase = c * 2 * QH;
+        for (int idx = threadIdx.x; idx < total; idx += BATCH_THREADS) {
+            const int a = idx / (L * SP);
+            const int rem = idx - a * (L * SP);
+            const int l = rem / SP;
+            const int j = rem - l * SP;
+            int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
+            if (a <= p.A && j < S) {
+                const int plo = l * S + j, phi = QH + l * S + j;
+                if (qbase + plo < Q.qlen)
+                    lo = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + plo] : (int)p.min_m) + pb;
+                if (qbase + phi < Q.qlen)
+                    hi = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + phi] : (int)p.min_m) + pb;
+            }
+            sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] =
+                (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+        }
+    };
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_unit = atomicAdd(p.counter, 1ull);
+        __syncthreads();  // s_unit visible; every group done with the last unit's profile
+        const int64_t u = (int64_t)s_unit;
+        if (u >= n_units)
+            break;
+        const int64_t t = u / p.n_queries;
+        const MultiQuery Q = p.queries[u - t * p.n_queries];
+        for (int kk = 0; kk < K; ++kk) {
+            const int64_t w = t * per_tile + (int64_t)kk * GPC + grp;
+            int seq = w < p.n_items ? p.order[w] : -1;
+            int64_t start = 0;
+            int len = 0;
+            if (seq >= 0) {
+                start = p.off[seq];
+                len = (int)(p.off[seq + 1] - start);
+                if (Q.qlen >= p.skip_len && len >= p.skip_len) {
+                    seq = -1;  // could overflow the packed lanes: the int32 launch scores it
+                    len = 0;
+                }
+            }
+            const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
+            int best = 0;
+            for (int c = 0; c < Q.C; ++c) {
+                if (Q.C > 1 || kk == 0) {  // a single-chunk profile is staged once per unit
+                    if (kk > 0 || c > 0)
+                        __syncthreads();  // every group is done with the staged profile
+                    stage(Q, c);
+                    __syncthreads();
+                }
+                const uint32_t mx = split_unit<L, S, D0, false, false, AC>(sprof, p.db, start, len, ncols, p.A,
+                                                                           p.o, p.e, p.one, c > 0, c + 1 < Q.C, bnd,
+                                                                           gl, nullptr, nullptr, nullptr, 0);
+                best = max(best, LaneQ16::score(mx, 0, k));
+            }
+            if (gl == 0 && seq >= 0)
+                p.scores[Q.row * p.row_stride + seq] = best;
+        }
+    }
+}
+
+// Single-chunk queries: every CTA walks the queries in order.  For each one
+// whose items are not all taken yet it stages the profile once, and its
+// warps pull sequences from that query's own counter exactly as the
+// per-query kernel does (longest first, no barrier between sequences); the
+// CTA's warps meet at a barrier only when the query's sequences run out,
+// where the remaining ones are the shortest.  Per query the work is the
+// per-query kernel's, without a launch or a tail of its own.
+template <int L, int S, bool D0, bool AC>
+__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC>::value)
+    sw_multi_phase_kernel(const MultiArgs p)
+{
+    constexpr int G = 32 / L;
+    constexpr int SP = SegPad<S, 4>::value;
+    constexpr int QH = L * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sprof = reinterpret_cast<uint32_t *>(smem_raw);
+    __shared__ int s_skip;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const int pb = split_pb<D0>(p.o);
+    const LaneQ16::K k = LaneQ16::consts_pb(p.o, p.e, S, p.one, pb);
+    const int total = (p.A + 2) * L * SP;
+    for (int qi = 0; qi < p.n_queries; ++qi) {
+        __syncthreads();  // every warp is done with the previous query's profile
+        if (threadIdx.x == 0)
+            s_skip = *reinterpret_cast<volatile unsigned long long *>(p.counter + qi) >=
+                     (unsigned long long)p.n_items;
+        __syncthreads();
+        if (s_skip)
+            continue;  // its sequences are all taken
+        const MultiQuery Q = p.queries[qi];
+        // stage the profile: virtual lanes l and L + l paired in one word;
+        // row A: an unknown residue (the smallest entry), row A+1: inert
+        for (int idx = threadIdx.x; idx < total; idx += BATCH_THREADS) {
+            const int a = idx / (L * SP);
+            const int rem = idx - a * (L * SP);
+            const int l = rem / SP;
+            const int j = rem - l * SP;
+            int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
+            if (a <= p.A && j < S) {
+                const int plo = l * S + j, phi = QH + l * S + j;
+                if (plo < Q.qlen)
+                    lo = (a < p.A ? (int)Q.prof[(size_t)a * 2 * QH + plo] : (int)p.min_m) + pb;
+                if (phi < Q.qlen)
+                    hi = (a < p.A ? (int)Q.prof[(size_t)a * 2 * QH + phi] : (int)p.min_m) + pb;
+            }
+            sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] =
+                (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+        }
+        __syncthreads();
+        int32_t *scores = p.scores + Q.row * p.row_stride;
+        for (;;) {
+            unsigned long long ubase = 0;
+            if (lane == 0)
+                ubase = atomicAdd(p.counter + qi, (unsigned long long)G);
+            ubase = __shfl_sync(MULTI_FULL, ubase, 0);
+            if ((int64_t)ubase >= p.n_items)
+                break;
+            const int64_t w = (int64_t)ubase + grp;
+            int seq = w < p.n_items ? p.order[w] : -1;
+            const int64_t start = seq >= 0 ? p.off[seq] : 0;
+            int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
+            if (seq >= 0 && Q.qlen >= p.skip_len && len >= p.skip_len) {
+                seq = -1;  // could overflow the packed lanes: the int32 launch scores it
+                len = 0;
+            }
+            const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
+            const uint32_t mx = split_unit<L, S, D0, false, false, AC>(sprof, p.db, start, len, ncols, p.A, p.o, p.e,
+                                                                       p.one, false, false, nullptr, gl);
+            if (gl == 0 && seq >= 0)
+                scores[seq] = LaneQ16::score(mx, 0, k);
+        }
+    }
+}
+
+// int32 lanes, 32 lanes per alignment: the pairs the packed launch leaves
+// (min(m, n) >= skip_len), over the first n_items entries of the order.
+template <class LT, int S>
+__global__ void __launch_bounds__(BATCH_THREADS) sw_multi_i32_kernel(const MultiArgs p)
+{
+    constexpr int L = 32;
+    constexpr int GPC = BATCH_THREADS / 32;
+    constexpr int QC = L * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int32_t *sprof = reinterpret_cast<int32_t *>(smem_raw);
+    __shared__ unsigned long long s_unit;
+
+    const int gl = threadIdx.x & 31;
+    const int grp = (int)(threadIdx.x >> 5);
+    const int64_t n_tiles = (p.n_items + GPC - 1) / GPC;
+    const int64_t n_units = n_tiles * p.n_queries;
+    int2 *bnd = p.bnd ? reinterpret_cast<int2 *>(p.bnd + ((int64_t)blockIdx.x * GPC + grp) * p.bnd_stride) : nullptr;
+    const int32_t *pbase[1] = {sprof};
+    const int64_t bstart[1] = {0};
+    unsigned long long lazy_steps = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_unit = atomicAdd(p.counter, 1ull);
+        __syncthreads();
+        const int64_t u = (int64_t)s_unit;
+        if (u >= n_units)
+            break;
+        const int64_t t = u / p.n_queries;
+        const MultiQuery Q = p.queries[u - t * p.n_queries];
+        const int64_t w = t * GPC + grp;
+        int seq = w < p.n_items ? p.order[w] : -1;
+        int64_t start[1] = {0};
+        int len[1] = {0};
+        if (seq >= 0) {
+            start[0] = p.off[seq];
+            len[0] = (int)(p.off[seq + 1] - start[0]);
+            if (!(Q.qlen >= p.skip_len && len[0] >= p.skip_len)) {
+                seq = -1;  // scored by the packed launch
+                len[0] = 0;
+            }
+        }
+        const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len[0]);
+        int best = 0;
+        for (int c = 0; c < Q.C; ++c) {
+            if (c > 0)
+                __syncthreads();
+            const int8_t *gprof = Q.prof + (size_t)c * p.A * QC;
+            const int qbase = c * QC;
+            stage_profile<LT, L, S>(sprof, p.A, p.o, threadIdx.x, BATCH_THREADS, [&](int a, int l, int j) {
+                if (qbase + l * S + j >= Q.qlen)
+                    return -1024;
+                return a < p.A ? (int)gprof[(size_t)a * QC + l * S + j] : (int)p.min_m;
+            });
+            __syncthreads();
+            const int32_t mx = striped_unit<LT, L, S, false>(pbase, p.db, start, len, ncols, p.A, p.o, p.e, p.one,
+                                                             c > 0, c + 1 < Q.C, bnd, gl, lazy_steps, nullptr,
+                                                             nullptr, bstart);
+            best = max(best, (int)mx);
+        }
+        if (gl == 0 && seq >= 0)
+            p.scores[Q.row * p.row_stride + seq] = best;
+    }
+}
+
+}  // namespace swg

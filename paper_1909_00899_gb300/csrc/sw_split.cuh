@@ -89,8 +89,10 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                                                int ncols, int A, int o, int e, uint32_t one, bool has_prev,
                                                bool has_next, int2 *bnd, int gl,
                                                unsigned long long *lazy_steps = nullptr, int *end_r = nullptr,
-                                               int *end_q = nullptr)
+                                               int *end_q = nullptr, int64_t bbase = -1)
 {
+    // boundary rows are indexed from bbase (default: the residues' start)
+    const int64_t bb = bbase >= 0 ? bbase : start;
     static_assert(!(LAZY && ENDS), "end cells: scan-F only");
     static_assert(!AC || (D0 && !LAZY && !ENDS), "always-corrected pass: D0 scan-F scores only");
     using LT = LaneQ16;
@@ -147,10 +149,13 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
         // chunk (raw packed values; their high halves belong to that chunk's
         // last position), converted once here: its X as a 16-bit value and
         // the F entering (lazy-F: as the pair (F, 0) that starts lane 0's
-        // pass; scan-F: as a 16-bit carry)
+        // pass; scan-F: as a 16-bit carry).  Packing the two high halves
+        // into one word would halve these bytes, but the extra permute per
+        // column measured 3-4 % slower on the long-query layouts, and the
+        // rows cost no time at these rates.
         uint32_t my_h16 = xinit16, my_f = LAZY ? k.xzero : (uint32_t)LT::BX;
         if (has_prev && r < len) {
-            const uint2 raw = reinterpret_cast<const uint2 *>(bnd)[start + r];
+            const uint2 raw = reinterpret_cast<const uint2 *>(bnd)[bb + r];
             my_h16 = raw.x >> 16;
             my_f = LAZY ? __byte_perm(raw.y, k.xzero, 0x5432) : raw.y >> 16;
         }
@@ -361,7 +366,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                     *lazy_steps += steps;
                 hlast = X[S - 1];
                 if (has_next && gl == L - 1 && rc < len)
-                    reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, fb);
+                    reinterpret_cast<uint2 *>(bnd)[bb + rc] = make_uint2(hlast, fb);
             } else {
                 // scan-F: the chunk boundary's F is lane 0's low-half carry
                 // (fetched here, after the pass, so that it holds no register
@@ -391,7 +396,7 @@ __device__ __forceinline__ uint32_t split_unit(const uint32_t *prof, const uint8
                            : LT::last_corr(X[S - 1], cin, k);
                 // the next chunk reads the high halves (this chunk's last position)
                 if (has_next && gl == L - 1 && rc < len)
-                    reinterpret_cast<uint2 *>(bnd)[start + rc] = make_uint2(hlast, x);
+                    reinterpret_cast<uint2 *>(bnd)[bb + rc] = make_uint2(hlast, x);
             }
         }
     }

@@ -4,8 +4,11 @@ with continuous batching.
 Requests arrive over time (for example a Poisson stream).  A request is
 admitted as soon as it has arrived, a stream slot is free and the device
 memory it needs (its score vector, its profile and, for queries longer than
-one chunk, the boundary rows between chunks) fits the memory budget next to
-the requests already running.  Admitted requests run concurrently on
+one chunk, the boundary rows between chunks) fits both the memory budget
+next to the requests already running and the memory the device has
+available right now (sw_mem_available: free memory plus the idle blocks of
+the stream-ordered pool the library allocates from), so other users of the
+GPU shrink what the server takes on.  Admitted requests run concurrently on
 separate CUDA streams (their kernels overlap on the device); completion is
 detected by polling an event, after which the scores are copied to pinned
 host memory and the request's memory returns to the budget.  Latency is
@@ -58,6 +61,7 @@ class Server:
         self.free_slots = collections.deque(self.slots)
         self.total_residues = int(db.offsets[-1].item())
         self.rejected = 0
+        self.waited_for_memory = 0  # admissions deferred because the device lacked the memory
 
     def request_bytes(self, m):
         """Device memory one request holds while it runs (its slot's score
@@ -125,6 +129,14 @@ class Server:
                     self.rejected += 1
                     continue
                 if self.in_use + need > self.budget:
+                    break
+                if need > sw.sw_mem_available():
+                    if not running:  # nothing of ours will free memory: refuse
+                        r = pending.popleft()
+                        r.done = now
+                        self.rejected += 1
+                        continue
+                    self.waited_for_memory += 1
                     break
                 r = pending.popleft()
                 self._admit(r, now)

@@ -34,7 +34,7 @@ EXPORTS = (
     "sw_probe_cell_rate", "sw_probe_cell_rate_pass", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_db_ends", "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats",
     "sw_align_batch_noalloc", "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends",
-    "sw_align_lazyf_pairs_lane",
+    "sw_align_lazyf_pairs_lane", "sw_multi_create", "sw_align_multi", "sw_multi_free", "sw_mem_available",
 )
 
 
@@ -97,6 +97,14 @@ def lib():
                                                 _vp]
         L.sw_align_lazyf_db_stats.restype = ctypes.c_int
         L.sw_align_lazyf_db_stats.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp, _vp]
+        L.sw_multi_create.restype = ctypes.c_int
+        L.sw_multi_create.argtypes = [_vp, _i32, _vp, _i32, _vp, ctypes.POINTER(_vp)]
+        L.sw_align_multi.restype = ctypes.c_int
+        L.sw_align_multi.argtypes = [_vp, _i32, _i32, _vp, _i64, _vp]
+        L.sw_multi_free.restype = ctypes.c_int
+        L.sw_multi_free.argtypes = [_vp]
+        L.sw_mem_available.restype = ctypes.c_int
+        L.sw_mem_available.argtypes = [ctypes.POINTER(_i64)]
         L.sw_stream_sync.restype = ctypes.c_int
         L.sw_stream_sync.argtypes = [_vp, _i64]
         L.sw_last_error.restype = ctypes.c_char_p
@@ -373,11 +381,72 @@ def sw_align_lazyf_db_stats(profile, db, gap_open, gap_extend, scores_out, lazy_
     return scores_out
 
 
+class Multi:
+    """A batch of profiled queries against one resident database
+    (sw_multi): keeps references to the profiles and the database, which
+    must stay alive while the handle exists."""
+
+    def __init__(self, profiles, db, stream=None, items_per_group=0):
+        self.profiles = list(profiles)
+        self.db = db
+        arr = (_vp * max(1, len(self.profiles)))(*[p.handle for p in self.profiles])
+        h = _vp()
+        _check(lib().sw_multi_create(arr, len(self.profiles), db.handle, int(items_per_group), _stream(stream),
+                                     ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().sw_multi_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sw_multi_create(profiles, db, items_per_group=0, stream=None):
+    return Multi(profiles, db, stream, items_per_group)
+
+
+def sw_multi_free(batch):
+    batch.free()
+
+
+def sw_align_multi(batch, gap_open, gap_extend, scores_out, stream=None):
+    """Scores of every query of the batch against the database: scores_out
+    is a 2-D int32 CUDA tensor [n_queries, >= n_db] (rows may be padded);
+    one persistent launch per layout, graph-capturable."""
+    if scores_out.dim() != 2 or scores_out.shape[0] < len(batch.profiles) or scores_out.shape[1] < batch.db.n:
+        raise ValueError("scores_out must be [n_queries, >= n_db]")
+    if scores_out.stride(1) != 1:
+        raise ValueError("scores_out rows must be contiguous")
+    if str(scores_out.dtype) != "torch.int32" or not scores_out.is_cuda:
+        raise TypeError("expected an int32 CUDA tensor")
+    _check(lib().sw_align_multi(batch.handle, int(gap_open), int(gap_extend), scores_out.data_ptr(),
+                                int(scores_out.stride(0)), _stream(stream)))
+    return scores_out
+
+
 def sw_plan_query(qlen, lane_type=SW_LANE_AUTO):
     """The plan a profile of qlen residues would get (host only)."""
     vals = [_i32() for _ in range(4)]
     _check(lib().sw_plan_query(int(qlen), int(lane_type), *[ctypes.byref(v) for v in vals]))
     return dict(lanes=vals[0].value, seg_len=vals[1].value, chunks=vals[2].value, lane_type=vals[3].value)
+
+
+def sw_mem_available():
+    """Bytes of device memory a new call could use now (free memory plus
+    the idle blocks of the device's stream-ordered pool)."""
+    out = _i64(0)
+    _check(lib().sw_mem_available(ctypes.byref(out)))
+    return int(out.value)
 
 
 def sw_stream_sync(stream=None, timeout_ms=60_000):

@@ -139,19 +139,163 @@ def test_graph_captured_ragged_batch(sw, small_db):
     rng = np.random.default_rng(2005)
     qlens = synth.lengths_loguniform(rng, 24, 32, 1500)
     queries = [synth.residues(rng, int(m), 20) for m in qlens]
-    out = torch.full((len(queries), h.n), -1, dtype=torch.int32, device="cuda")
-    ba = BatchAligner(h, M, 11, 1).prepare(queries, out)
-    out.fill_(-1)
-    ba.run()
+    for mode in ("multi", "per_query"):
+        out = torch.full((len(queries), h.n), -1, dtype=torch.int32, device="cuda")
+        ba = BatchAligner(h, M, 11, 1, mode=mode).prepare(queries, out)
+        assert (ba.multi is not None) == (mode == "multi")
+        out.fill_(-1)
+        ba.run()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for i, q in enumerate(queries):
+            np.testing.assert_array_equal(got[i], oracle.gotoh_batch(q, db, off, M, 11, 1),
+                                          err_msg="query %d, %s" % (i, mode))
+        out.fill_(-1)
+        ba.run()  # replays give the same result
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), got)
+        ba.free()
+
+
+def _multi_case(sw, M, o, e, seqs, queries, layouts):
+    """sw_align_multi on a padded score matrix, eagerly and replayed from a
+    CUDA graph, every row against the oracle."""
+    from helpers import pack_list
+    db, off = pack_list(seqs)
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    profs = []
+    for q, lay in zip(queries, layouts):
+        if lay is None:
+            profs.append(sw.Profile(q, M))
+        else:
+            profs.append(sw.Profile(q, M, sw.SW_LANE_I16X2Q, lanes=lay[0], seg_len=lay[1]))
+    batch = sw.Multi(profs, h)
+    n = h.n
+    out = torch.full((len(queries), n + 5), -7, dtype=torch.int32, device="cuda")  # padded rows
+    sw.sw_align_multi(batch, o, e, out)
     torch.cuda.synchronize()
     got = out.cpu().numpy()
     for i, q in enumerate(queries):
-        np.testing.assert_array_equal(got[i], oracle.gotoh_batch(q, db, off, M, 11, 1), err_msg="query %d" % i)
+        want = oracle.gotoh_batch(q, db, off, M, o, e)
+        np.testing.assert_array_equal(got[i, :n], want, err_msg="query %d (m=%d, layout %s)"
+                                      % (i, len(q), layouts[i]))
+        assert np.all(got[i, n:] == -7)  # padding untouched
+    # captured into a graph and replayed: the same scores
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="thread_local"):
+        sw.sw_align_multi(batch, o, e, out, stream=st)
     out.fill_(-1)
-    ba.run()  # replays give the same result
+    g.replay()
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(out.cpu().numpy(), got)
-    ba.free()
+    np.testing.assert_array_equal(out.cpu().numpy()[:, :n], got[:, :n])
+    batch.free()
+    for p in profs:
+        p.free()
+    h.free()
+    return got[:, :n], db, off
+
+
+def test_long_query_on_db_handle_captures_into_a_graph(sw, small_db):
+    """A 5000-residue query (several chunks, boundary rows sized from the
+    handle's cached residue count) through sw_align_db is captured into a
+    CUDA graph with no host synchronisation, and the replay equals the
+    oracle; single-chunk sw_align_batch calls capture too."""
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    rng = np.random.default_rng(2013)
+    q_long = synth.residues(rng, 5000, 20)
+    q_short = synth.residues(rng, 400, 20)
+    p_long = sw.Profile(q_long, M)
+    p_short = sw.Profile(q_short, M)
+    assert p_long.plan()["chunks"] > 1 and p_short.plan()["chunks"] == 1
+    a = torch.full((h.n,), -7, dtype=torch.int32, device="cuda")
+    b = torch.full((h.n,), -7, dtype=torch.int32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):  # eager once (kernel attributes, pool)
+        sw.sw_align_db(p_long, h, 11, 1, a, stream=st)
+        sw.sw_align_batch(p_short, db_d, off_d, 11, 1, b, stream=st)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="thread_local"):
+        sw.sw_align_db(p_long, h, 11, 1, a, stream=st)
+        sw.sw_align_batch(p_short, db_d, off_d, 11, 1, b, stream=st)
+    a.fill_(-1)
+    b.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.cpu().numpy(), oracle.gotoh_batch(q_long, db, off, M, 11, 1))
+    np.testing.assert_array_equal(b.cpu().numpy(), oracle.gotoh_batch(q_short, db, off, M, 11, 1))
+    p_long.free()
+    p_short.free()
+    h.free()
+
+
+def test_batched_launch_every_layout_exact(sw):
+    """One persistent launch per layout over every (query, tile) unit:
+    queries on every split layout of 16+ virtual lanes (one and several
+    chunks, the chunk boundary rows in per-group slots), empty and
+    one-residue queries and sequences, copies of long queries planted in
+    long sequences (pairs whose score could pass the packed lanes' range
+    go to the int32 launch, here above 28,543), scores into padded rows."""
+    rng = np.random.default_rng(2010)
+    M = synth.protein_matrix(rng)
+    lens = np.concatenate([[0, 1, 2, 5], synth.lengths_lognormal(rng, 150, 300, 0.76, 20, 3000)])
+    seqs = [synth.residues(rng, int(x), 20) for x in lens]
+    layouts = [(16, 8), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (32, 40), (64, 8), (64, 16),
+               (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)]
+    queries, lays = [], []
+    for k, lay in enumerate(layouts):
+        for m in (max(1, lay[0] * lay[1] - 3), 2 * lay[0] * lay[1] + 5):  # one chunk, three chunks
+            queries.append(synth.residues(rng, int(m), 20))
+            lays.append(lay)
+    long_q = synth.residues(rng, 6000, 20)
+    queries += [np.zeros(0, np.uint8), synth.residues(rng, 1, 20), synth.residues(rng, 2700, 20), long_q]
+    lays += [None, None, None, None]
+    seqs.append(np.concatenate([synth.residues(rng, 30, 20), long_q[1000:5200], synth.residues(rng, 20, 20)]))
+    seqs.append(np.concatenate([queries[-2][100:2650], synth.residues(rng, 400, 20)]))
+    got, db, off = _multi_case(sw, M, 11, 1, seqs, queries, lays)
+    assert got[-1, -2] > 28543  # scored by the int32 launch
+    assert got[-2, -1] > 2550 * 4
+
+
+def test_batched_launch_general_pass_and_dna(sw):
+    """The batched launch with mismatch scores below -o (the general
+    corrected pass) and with DNA scoring (most h below zero: the always-
+    corrected pass's floor on the diagonal), query-side insertions across
+    many lanes and chunks."""
+    from helpers import gap_adversary
+    rng = np.random.default_rng(2011)
+    queries, refs = gap_adversary(rng, 4, 20, ylo=60, yhi=500)
+    refs += [synth.residues(rng, int(n), 4) for n in (1, 7, 900, 2500)]
+    queries = queries[:6] + [synth.residues(rng, n, 4) for n in (70, 700, 2100, 4000)]
+    for o, e, mm in ((6, 1, -4), (3, 1, -5), (5, 5, -2)):
+        M = synth.dna_matrix(match=2, mismatch=mm)
+        _multi_case(sw, M, o, e, refs, queries, [None] * len(queries))
+
+
+def test_batched_launch_rejects_what_it_cannot_run(sw, small_db):
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    q = synth.residues(np.random.default_rng(2012), 300, 20)
+    p32 = sw.Profile(q, M, sw.SW_LANE_I32)
+    with pytest.raises(sw.SwError):
+        sw.Multi([p32], h)  # not the split lane type
+    pa = sw.Profile(q, M)
+    batch = sw.Multi([pa], h)
+    out = torch.zeros((1, h.n), dtype=torch.int32, device="cuda")
+    with pytest.raises(sw.SwError) as ex:
+        sw.sw_align_multi(batch, 200, 1, out)  # gap open beyond the packed lanes
+    assert ex.value.code == sw.SW_ERR_RANGE
+    with pytest.raises(sw.SwError):
+        sw.sw_align_multi(batch, 11, 12, out)  # e > o
+    batch.free()
+    p32.free()
+    pa.free()
 
 
 def test_autotuner_table_is_exact(sw, small_db):
@@ -174,6 +318,44 @@ def test_autotuner_table_is_exact(sw, small_db):
     for i, q in enumerate(queries):
         np.testing.assert_array_equal(got[i], oracle.gotoh_batch(q, db, off, M, 11, 1))
     ba.free()
+
+
+def test_serving_admits_by_available_device_memory(sw, small_db, monkeypatch):
+    """Admission also checks the memory the device has now: with the query
+    reporting too little, requests wait while others of the server run and
+    are refused when nothing of its own is running to free memory; with the
+    real query every request is served, and sw_mem_available is at most the
+    device's total."""
+    from paper_1909_00899_gb300 import serve
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    rng = np.random.default_rng(2014)
+    queries = [synth.residues(rng, int(m), 20) for m in (60, 300, 900, 120)]
+    avail = sw.sw_mem_available()
+    assert 0 < avail <= torch.cuda.get_device_properties(0).total_memory
+    srv = serve.Server(h, M, 11, 1, slots=2)
+    reqs = srv.run(queries)
+    assert srv.rejected == 0 and all(r.scores is not None for r in reqs)
+    # a device that has only a few bytes left: nothing can be admitted
+    monkeypatch.setattr(serve.sw, "sw_mem_available", lambda: 1024)
+    srv2 = serve.Server(h, M, 11, 1, slots=2)
+    reqs2 = srv2.run(queries)
+    assert srv2.rejected == len(queries) and all(r.scores is None for r in reqs2)
+    # memory short only while the first request runs: the others wait, then run
+    state = {"calls": 0}
+
+    def flaky():
+        state["calls"] += 1
+        return avail if state["calls"] == 1 or srv3.in_use == 0 else 1024
+
+    monkeypatch.setattr(serve.sw, "sw_mem_available", flaky)
+    srv3 = serve.Server(h, M, 11, 1, slots=4)
+    reqs3 = srv3.run(queries)
+    assert srv3.rejected == 0 and srv3.waited_for_memory > 0
+    for a, b in zip(reqs, reqs3):
+        np.testing.assert_array_equal(a.scores, b.scores)
+    h.free()
 
 
 def test_serving_results_same_alone_and_in_the_mix(sw, small_db):

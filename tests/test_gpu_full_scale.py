@@ -37,7 +37,12 @@ def scale():
     return synth.workload_protein_scale()
 
 
-def test_scale_step_sampled_and_properties(sw, scale):
+@pytest.mark.parametrize("lane", ["auto", "i32"])
+def test_scale_step_sampled_and_properties(sw, scale, lane):
+    """The benchmark step at full size on the automatic lanes (split s16x2
+    with int32 rescore) and on int32 lanes throughout (the plain method's
+    own lane type, which the benchmark times beside it)."""
+    lane_type = {"auto": sw.SW_LANE_AUTO, "i32": sw.SW_LANE_I32}[lane]
     w = scale
     M, o, e = w["M"], w["o"], w["e"]
     n = len(w["off"]) - 1
@@ -53,7 +58,7 @@ def test_scale_step_sampled_and_properties(sw, scale):
     for i, q in enumerate(w["queries"]):
         st = side[i]
         st.wait_event(fork)
-        p = sw.Profile(q, M, sw.SW_LANE_AUTO, stream=st)
+        p = sw.Profile(q, M, lane_type, stream=st)
         sw.sw_align_batch(p, db_d, off_d, o, e, scan[i], stream=st)
         profs.append(p)
     torch.cuda.synchronize()
@@ -65,7 +70,7 @@ def test_scale_step_sampled_and_properties(sw, scale):
     for i, q in enumerate(w["queries"]):
         got = scan[i].cpu().numpy()
         want = oracle.gotoh_batch(q, sub_db, sub_off, M, o, e)
-        np.testing.assert_array_equal(got[ids], want, err_msg="m=%d" % len(q))
+        np.testing.assert_array_equal(got[ids], want, err_msg="m=%d lane=%s" % (len(q), lane))
         # every output: 0 <= score <= max(M) * min(m, n)
         assert got.min() >= 0
         assert np.all(got <= maxdiag * np.minimum(len(q), lens))
@@ -114,8 +119,8 @@ def test_ragged_batch_full_size_sampled(sw):
     """The ragged batch at its full database size (200k log-normal
     sequences, 80 M residues) in the benchmark's launch configuration:
     length-stratified queries from the 10,000 (32..4096), an autotuned
-    layout per length bin, every alignment in one graph replayed over four
-    streams.  Sampled outputs against the oracle (the longest sequences
+    split layout per length bin, one batched launch per layout (and the
+    int32 launch of the longest pairs) in one graph.  Sampled outputs against the oracle (the longest sequences
     included), every output against the direct database call and within
     0 <= score <= max(M) * min(m, n)."""
     from paper_1909_00899_gb300 import autotune
@@ -129,9 +134,10 @@ def test_ragged_batch_full_size_sampled(sw):
     queries = [synth.residues(np.random.default_rng([5, int(i)]), int(qlens_all[i]), 20) for i in pick]
     db_d, off_d = torch.from_numpy(db).cuda(), torch.from_numpy(off).cuda()
     h = sw.Database(db_d, off_d)
-    table = autotune.tune(h, M, 11, 1, lengths=[48, 400, 3200], reps=1)
+    table = autotune.tune(h, M, 11, 1, lengths=[48, 400, 3200], reps=1, lanes=(sw.SW_LANE_I16X2Q,))
     out = torch.full((len(queries), h.n), -7, dtype=torch.int32, device="cuda")
     ba = BatchAligner(h, M, 11, 1, table=table, streams=4).prepare(queries, out)
+    assert ba.multi is not None  # one batched launch per layout
     ba.run()
     torch.cuda.synchronize()
     got = out.cpu().numpy()
