@@ -33,7 +33,9 @@ if ROOT not in sys.path:
 QLENS = (128, 512, 2048, 5000)
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
 # capture of that launch; None while the kernel has changed since then.
-NCU_TRAFFIC = None
+NCU_TRAFFIC = {"bytes_per_launch": 51.398656e6 + 268.339968e6,
+               "kernel": "sw_split_kernel<16, 40, true, false, false, false, true>",
+               "launch": "m=5000 chunk 0 vs 100k sequences (ncu --set full)"}
 METRIC = "GCUPS scan-F (bit-exact) vs lazy-F"
 PROBE_ITERS = 1 << 19  # plain-pass probe: about 0.5 s on every SM
 WORKLOAD = ("protein queries m in {128,512,2048,5000} vs 100k db seqs, log-normal lengths "
