@@ -229,10 +229,14 @@ def run_reference(args):
         if k >= args.warmup:
             vals.append(cb)
     v = statistics.median([c["value"] for c in vals])
+    workload = WORKLOAD
+    if world > 1:  # the same description as the sharded GPU arm's
+        workload += (", %d ranks: a database of %d sequences sharded by length bin, %d per rank"
+                     % (world, args.n_db * world, args.n_db))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "config": {"workload": workload, "l2": "n/a (host)"},
             "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"],
                              "value": v, "unit": "GCUPS"},
             "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -373,7 +377,7 @@ def main():
     # correctness spot check against the oracle on a sample (not timed)
     check = None if args.quick else sample_check(wg, outs, step, rank, shard_ids)
 
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     total_ms = timed(args.steps)
     clocks = sampler.stop()
@@ -450,7 +454,7 @@ def main():
     i_dom = QLENS.index(max(QLENS))
     plan = plans[i_dom]
     cells_per_op = {1: 1, 2: 2, 3: 4, 4: 2}[plan["lane_type"]]
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     # integer ALU pipe: 16 lanes/clk per SM sub-partition, 4 per SM
     peak_alu = sms * 64 * mhz * 1e6 / (6.0 / cells_per_op) / 1e9
@@ -472,7 +476,7 @@ def main():
     # long enough (about 0.5 s) to carry its own clock record.  The
     # correction and scan the method adds count against the kernel, not in
     # the denominator.  The unit-count figure is kept as peak_model.
-    psampler = ClockSampler(local)
+    psampler = ClockSampler(torch.cuda.current_device())
     psampler.start()
     probe = sw.sw_probe_cell_rate(plan["lane_type"], PROBE_ITERS) / 1e9
     probe_clocks = psampler.stop()
