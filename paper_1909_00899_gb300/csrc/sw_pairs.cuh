@@ -163,11 +163,13 @@ int launch_pairs_inst(const PairArgs &a, const int32_t *list, const int32_t *cou
 // shared memory, row A the unknown residue, row A+1 inert.  ENDS: also the
 // end cell of each pair's best alignment (1-based, -1 when the score is 0).
 // LAZY: the lazy-F loop instead of the scan (the comparison on the same layout).
-template <int L, int S, bool D0, bool ENDS = false, bool LAZY = false>
+// AC: scan-F scores with the always-corrected pass (sw_split.cuh).
+template <int L, int S, bool D0, bool ENDS = false, bool LAZY = false, bool AC = false>
 __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, const int32_t *__restrict__ list,
                                                              const int32_t *__restrict__ count_dev, int64_t n_list)
 {
     static_assert(!(ENDS && LAZY), "end cells: scan-F only");
+    static_assert(!AC || (D0 && !ENDS && !LAZY), "always-corrected pass: D0 scan-F scores");
     unsigned long long lazy_steps = 0;
     constexpr int SP = SegPad<S, 4>::value;
     constexpr int QH = L * S;  // positions per half
@@ -239,8 +241,8 @@ __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, c
                 p.r_end[pid[0]] = sc > 0 ? er + 1 : -1;
             }
         } else {
-            const uint32_t mx = split_unit<L, S, D0, LAZY>(gprof, p.r, start, len, ncols, A, p.o, p.e, p.one, false,
-                                                           false, nullptr, gl, &lazy_steps);
+            const uint32_t mx = split_unit<L, S, D0, LAZY, false, AC>(gprof, p.r, start, len, ncols, A, p.o, p.e,
+                                                                      p.one, false, false, nullptr, gl, &lazy_steps);
             if (gl == 0)
                 write_scores<LaneQ16>(mx, k, pid, false, p.flag_thresh, p.scores);
         }
@@ -251,11 +253,11 @@ __global__ void __launch_bounds__(256) sw_pairs_split_kernel(const PairArgs p, c
         atomicAdd(p.lazy_steps, lazy_steps);
 }
 
-template <int L, int S, bool D0, bool ENDS = false, bool LAZY = false>
+template <int L, int S, bool D0, bool ENDS = false, bool LAZY = false, bool AC = false>
 int launch_pairs_split_inst(const PairArgs &a, const int32_t *list, const int32_t *count_dev, int64_t n_hint,
                             int num_sms, cudaStream_t st)
 {
-    auto kern = sw_pairs_split_kernel<L, S, D0, ENDS, LAZY>;
+    auto kern = sw_pairs_split_kernel<L, S, D0, ENDS, LAZY, AC>;
     const size_t per_warp = (size_t)32 * (a.A + 2) * SegPad<S, 4>::value * 4;
     int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
     const size_t smem = per_warp * warps;
