@@ -313,16 +313,22 @@ int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
  *    queries in order, stages each one's profile once and pulls its
  *    sequences, longest first, from the query's own counter, as the
  *    per-query kernel does.
- *  - Queries of several chunks (per layout, one launch): work units are
- *    (query, tile of consecutive sequences of the length order),
- *    tile-major so that the longest tiles of every query go first;
- *    items_per_group (1..64, 0: the library's default, 4) sets the tile:
- *    each lane group of a CTA takes that many sequences per unit; a unit
- *    runs all chunks of its query inside one CTA, with each lane group's
- *    chunk boundary row in its own slot of max_len columns (no
- *    residue-sized rows per query).
- *  - Packed lanes cannot overflow there: pairs with
- *    min(m, n) * max(M) >= the s16x2 rescore threshold go to int32 lanes.
+ *  - Queries of several chunks (per layout, one launch): every CTA walks
+ *    the (query, chunk) phases in order, staging each chunk's profile once
+ *    and pulling the phase's sequences from its own counter, with one
+ *    chunk boundary row per database residue (8 bytes each, allocated by
+ *    sw_multi_create) reused by every query; a sequence is aligned in a
+ *    phase only after the previous phase finished it (a per-sequence mark;
+ *    the wait is bounded, see sw_multi_status).
+ *  - items_per_group (1..64; 0: the phase walk above) asks instead for
+ *    the fused-chunk kernel on queries of several chunks: units of (query,
+ *    tile of that many sequences per lane group), each running all chunks
+ *    of its query inside one CTA with every group's boundary row in its
+ *    own slot of max_len columns (no residue-sized rows).
+ *  - Overflow: the packed launches score every pair; only pairs with
+ *    min(m, n) * max(M) >= the s16x2 rescore threshold can overflow, and
+ *    the int32 launch walks those and rescores the ones whose packed score
+ *    reached the threshold (none, on random protein data).
  *  - profiles: host array of n_queries profiles, all built with the same
  *    substitution matrix on SW_LANE_I16X2Q (or SW_LANE_AUTO, which chooses
  *    it) with layouts of 16 or more virtual lanes; they and the database
@@ -341,6 +347,11 @@ int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries,
 int sw_align_multi(const sw_multi *batch, int32_t gap_open, int32_t gap_extend,
                    int32_t *scores_out, int64_t row_stride, void *cuda_stream);
 int sw_multi_free(sw_multi *batch);
+/* The batch handle's status word, then cleared: 0, or 1 when a bounded
+ * wait of the (query, chunk) phase walk gave up (about a second) since the
+ * last read, in which case some scores of those calls may be wrong.
+ * Synchronises cuda_stream. */
+int sw_multi_status(const sw_multi *batch, int32_t *status_out, void *cuda_stream);
 
 /*
  * sw_align_batch_noalloc — sw_align_batch (same arguments, results and

@@ -193,14 +193,22 @@ struct MultiArgs {
     const int64_t *off;
     const int32_t *order;   // sequence ids by length, longest first
     int64_t n_items;        // entries of order covered
-    int32_t skip_len;       // pairs with min(query length, sequence length) >= skip_len:
-                            // skipped by the packed launch, the only ones of the int32 launch
+    int32_t skip_len;       // pairs with min(query length, sequence length) >= skip_len: the
+                            // int32 launch's candidates (only they can overflow the packed lanes)
+    int32_t flag_thresh;    // the int32 launch rescores candidates whose packed score reached it
     int32_t *scores;        // row-major [query][row_stride]
     int64_t row_stride;
     int32_t k_items;        // sequences per lane group per unit (the tile is k_items x groups per CTA)
     unsigned long long *counter;  // unit counter (phase kernel: one per query), zero at launch
     uint32_t *bnd;          // per-group boundary-row slots (32-bit words), null when C == 1 throughout
     int64_t bnd_stride;     // words per group slot
+    // the chunk-phase kernel: boundary rows of every database residue
+    // (int2, indexed offsets[seq] + r), the last phase each sequence of the
+    // order finished (-1 at launch), and a status word set when a bounded
+    // wait gave up (0 at launch)
+    int2 *rows;
+    int32_t *done;
+    int32_t *status;
 };
 
 // multi-query launchers (sw_k_multi*.cu): split s16x2 layouts (virtual lanes
@@ -208,10 +216,11 @@ struct MultiArgs {
 // counter is one per query, else the fused-chunk kernel) and the int32
 // layouts 32 x {8, 16, 32} of the pairs that could overflow the packed
 // lanes; grid is fixed by the caller (its boundary slots are sized for it).
-int launch_multi_split(int VL, int S, bool phase, const MultiArgs &a, int grid, cudaStream_t st);
+constexpr int MULTI_FUSED = 0, MULTI_PHASE = 1, MULTI_CHUNKS = 2;
+int launch_multi_split(int VL, int S, int kind, const MultiArgs &a, int grid, cudaStream_t st);
 int launch_multi_i32(int S, const MultiArgs &a, int grid, cudaStream_t st);
 // CTAs per SM the launch runs with (0 for a layout without a kernel)
-int multi_split_blocks_per_sm(int VL, int S, bool phase, bool d0, int A);
+int multi_split_blocks_per_sm(int VL, int S, int kind, bool d0, int A);
 int multi_i32_blocks_per_sm(int S, bool d0, int A);
 // groups (one item each) per CTA of a layout of `lanes` virtual lanes (the
 // int32 kernels' 32 lanes per alignment count as 64: one group per warp)

@@ -7,7 +7,7 @@ namespace swg {
 
 int multi_split_narrow(int VL_, int S_, bool d0, const MultiArgs *a, int grid, cudaStream_t st, int *per_sm, int A)
 {
-    constexpr bool PHASE = false;
+    constexpr int KIND = MULTI_FUSED;
     SWG_MULTI_CASE(16, 8)
     SWG_MULTI_CASE(32, 8)
     SWG_MULTI_CASE(32, 12)

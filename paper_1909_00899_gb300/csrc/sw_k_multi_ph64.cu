@@ -7,7 +7,7 @@ namespace swg {
 
 int multi_phase_wide(int VL_, int S_, bool d0, const MultiArgs *a, int grid, cudaStream_t st, int *per_sm, int A)
 {
-    constexpr bool PHASE = true;
+    constexpr int KIND = MULTI_PHASE;
     SWG_MULTI_CASE(64, 8)
     SWG_MULTI_CASE(64, 16)
     SWG_MULTI_CASE(64, 20)

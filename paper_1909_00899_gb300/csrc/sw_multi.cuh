@@ -27,12 +27,17 @@
 // is the per-query kernel's (measured 5-20 % faster than the fused-chunk
 // structure on those layouts).
 //
-// Packed lanes never overflow here: an alignment of m x n cells scores at
-// most max(M) * min(m, n), so pairs with min(m, n) >= skip_len (the packed
-// lane's rescore threshold over max(M)) are left to a second launch on int32
-// lanes, which takes only those pairs.  They are the longest database
-// sequences against the longest queries, a prefix of the length order.
+// Overflow: the packed launches score every pair; a packed lane's running
+// maximum never decreases, so a pair whose value left the lane range ends at
+// or above the rescore threshold.  Only pairs with min(m, n) >= skip_len (the
+// threshold over max(M); an alignment of m x n cells scores at most
+// max(M) * min(m, n)) can get there: the longest database sequences against
+// the longest queries, a prefix of the length order.  A second launch on
+// int32 lanes walks exactly those candidates and rescores the ones whose
+// packed score reached the threshold, skipping units that have none.
 #pragma once
+#include <cuda/atomic>
+
 #include "sw_split.cuh"
 
 namespace swg {
@@ -106,10 +111,6 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
             if (seq >= 0) {
                 start = p.off[seq];
                 len = (int)(p.off[seq + 1] - start);
-                if (Q.qlen >= p.skip_len && len >= p.skip_len) {
-                    seq = -1;  // could overflow the packed lanes: the int32 launch scores it
-                    len = 0;
-                }
             }
             const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
             int best = 0;
@@ -193,11 +194,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
             const int64_t w = (int64_t)ubase + grp;
             int seq = w < p.n_items ? p.order[w] : -1;
             const int64_t start = seq >= 0 ? p.off[seq] : 0;
-            int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
-            if (seq >= 0 && Q.qlen >= p.skip_len && len >= p.skip_len) {
-                seq = -1;  // could overflow the packed lanes: the int32 launch scores it
-                len = 0;
-            }
+            const int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
             const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
             const uint32_t mx = split_unit<L, S, D0, false, false, AC>(sprof, p.db, start, len, ncols, p.A, p.o, p.e,
                                                                        p.one, false, false, nullptr, gl);
@@ -207,8 +204,144 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
     }
 }
 
-// int32 lanes, 32 lanes per alignment: the pairs the packed launch leaves
-// (min(m, n) >= skip_len), over the first n_items entries of the order.
+// Queries of several chunks: the phase walk over (query, chunk) phases.
+// Every CTA walks the phases in order (query by query, chunk by chunk),
+// stages each phase's profile chunk once and pulls its sequences, longest
+// first, from the phase's own counter, as the per-query chunk launches do.
+// The chunk boundary rows are one row of every database residue, reused by
+// every query: phase (q, c) reads what (q, c - 1) wrote and writes what
+// (q, c + 1) reads, in place, as the per-query launches do.  Each sequence
+// of the order carries the last phase that finished it: before a group
+// aligns sequence w in phase P it waits until w is done with phase P - 1
+// (acquire), and after it, publishes P (release, after the boundary row and
+// the score).  A CTA enters phase P only once P - 1's counter is exhausted,
+// so every sequence of P - 1 is already held by a resident warp of another
+// CTA (this CTA's warps finished theirs at the phase barrier), and as both
+// phases run longest first, P reaches a sequence long after P - 1 finished
+// it: the wait is a formality with no cycle.  It is bounded all the same
+// (about a second), after which the group sets the status word and goes on.
+constexpr int MULTI_WAIT_LIMIT = 1 << 22;  // polls of about 256 ns
+
+template <int L, int S, bool D0, bool AC>
+__global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC>::value)
+    sw_multi_chunks_kernel(const MultiArgs p)
+{
+    constexpr int G = 32 / L;
+    constexpr int SP = SegPad<S, 4>::value;
+    constexpr int QH = L * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sprof = reinterpret_cast<uint32_t *>(smem_raw);
+    __shared__ int s_skip;
+    // the phase's query, kept in shared memory: the cell loop needs every
+    // register (the S = 40 layouts spilled with it in registers)
+    __shared__ MultiQuery s_q;
+    // each group's item and sequence, parked over the cell loop
+    __shared__ long long s_w[(BATCH_THREADS / 32) * G];
+    __shared__ int s_seq[(BATCH_THREADS / 32) * G];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const int gslot = (int)(threadIdx.x >> 5) * G + grp;
+    const int pb = split_pb<D0>(p.o);
+    const int total = (p.A + 2) * L * SP;
+    int phase = 0;  // running (query, chunk) phase number
+    for (int qi = 0; qi < p.n_queries; ++qi) {
+        __syncthreads();  // every thread is done with the previous query's record
+        if (threadIdx.x == 0)
+            s_q = p.queries[qi];
+        __syncthreads();
+        const int nchunks = s_q.C;
+        for (int c = 0; c < nchunks; ++c, ++phase) {
+            __syncthreads();  // every warp is done with the previous phase's profile
+            if (threadIdx.x == 0)
+                s_skip = *reinterpret_cast<volatile unsigned long long *>(p.counter + phase) >=
+                         (unsigned long long)p.n_items;
+            __syncthreads();
+            if (s_skip)
+                continue;  // its sequences are all taken
+            // stage chunk c: virtual lanes l and L + l paired in one word;
+            // row A: an unknown residue (the smallest entry), row A+1: inert
+            {
+                const int8_t *gprof = s_q.prof + (size_t)c * p.A * 2 * QH;
+                const int qbase = c * 2 * QH;
+                const int qlen = s_q.qlen;
+                for (int idx = threadIdx.x; idx < total; idx += BATCH_THREADS) {
+                    const int a = idx / (L * SP);
+                    const int rem = idx - a * (L * SP);
+                    const int l = rem / SP;
+                    const int j = rem - l * SP;
+                    int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
+                    if (a <= p.A && j < S) {
+                        const int plo = l * S + j, phi = QH + l * S + j;
+                        if (qbase + plo < qlen)
+                            lo = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + plo] : (int)p.min_m) + pb;
+                        if (qbase + phi < qlen)
+                            hi = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + phi] : (int)p.min_m) + pb;
+                    }
+                    sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] =
+                        (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+                }
+            }
+            __syncthreads();
+            for (;;) {
+                unsigned long long ubase = 0;
+                if (lane == 0)
+                    ubase = atomicAdd(p.counter + phase, (unsigned long long)G);
+                ubase = __shfl_sync(MULTI_FULL, ubase, 0);
+                if ((int64_t)ubase >= p.n_items)
+                    break;
+                const int64_t w = (int64_t)ubase + grp;
+                const int seq = w < p.n_items ? p.order[w] : -1;
+                const int64_t start = seq >= 0 ? p.off[seq] : 0;
+                const int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
+                // wait until this sequence is done with the previous phase
+                if (w < p.n_items && phase > 0 && gl == 0) {
+                    cuda::atomic_ref<int32_t, cuda::thread_scope_device> d(p.done[w]);
+                    int it = 0;
+                    while (d.load(cuda::memory_order_acquire) < phase - 1) {
+                        if (++it > MULTI_WAIT_LIMIT) {
+                            atomicExch(p.status, 1);
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+                if (gl == 0) {
+                    s_w[gslot] = w < p.n_items ? w : -1;
+                    s_seq[gslot] = seq;
+                }
+                __syncwarp(MULTI_FULL);
+                const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
+                const uint32_t mx = split_unit<L, S, D0, false, false, AC>(sprof, p.db, start, len, ncols, p.A, p.o,
+                                                                           p.e, p.one, c > 0, c + 1 < nchunks,
+                                                                           p.rows, gl);
+                __syncwarp(MULTI_FULL);  // the group's boundary-row stores come before the mark
+                if (gl == 0) {
+                    const long long wi = s_w[gslot];
+                    const int sq = s_seq[gslot];
+                    if (sq >= 0) {
+                        // the maximum over the chunks so far (chunk c - 1 wrote
+                        // before it published its mark); h-space bias BX + pb - o
+                        const int sc = max((int)(int16_t)(mx & 0xffffu), (int)(int16_t)(mx >> 16)) -
+                                       (LaneQ16::BX + pb - p.o);
+                        int32_t *dst = p.scores + s_q.row * p.row_stride + sq;
+                        *dst = c > 0 ? max(sc, *dst) : sc;
+                    }
+                    if (wi >= 0) {
+                        __threadfence();
+                        cuda::atomic_ref<int32_t, cuda::thread_scope_device> d(p.done[wi]);
+                        d.store(phase, cuda::memory_order_release);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// int32 lanes, 32 lanes per alignment: the candidates that could overflow
+// the packed lanes (min(m, n) >= skip_len, over the first n_items entries
+// of the order) whose packed score reached the rescore threshold; a unit
+// with none of them is skipped before its profile is staged.
 template <class LT, int S>
 __global__ void __launch_bounds__(BATCH_THREADS) sw_multi_i32_kernel(const MultiArgs p)
 {
@@ -244,11 +377,15 @@ __global__ void __launch_bounds__(BATCH_THREADS) sw_multi_i32_kernel(const Multi
         if (seq >= 0) {
             start[0] = p.off[seq];
             len[0] = (int)(p.off[seq + 1] - start[0]);
-            if (!(Q.qlen >= p.skip_len && len[0] >= p.skip_len)) {
-                seq = -1;  // scored by the packed launch
+            // a candidate whose packed score stayed below the threshold is exact
+            if (!(Q.qlen >= p.skip_len && len[0] >= p.skip_len) ||
+                p.scores[Q.row * p.row_stride + seq] < p.flag_thresh) {
+                seq = -1;
                 len[0] = 0;
             }
         }
+        if (!__syncthreads_or(seq >= 0))
+            continue;  // nothing to rescore in this unit
         const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len[0]);
         int best = 0;
         for (int c = 0; c < Q.C; ++c) {

@@ -20,9 +20,11 @@ namespace {
 
 struct MultiBin {
     int VL = 0, S = 0;   // split layout: virtual lanes x positions
-    bool phase = false;  // single-chunk queries: the phase kernel
+    bool phase = false;  // single-chunk queries (the phase kernel), else several chunks
+    int kind = 0;        // MULTI_PHASE, MULTI_CHUNKS or MULTI_FUSED
     int nq = 0;          // queries of the bin
-    int64_t cnt = 0;     // first of its counters (phase: one per query)
+    int64_t chunks = 0;  // chunks of all its queries
+    int64_t cnt = 0;     // first of its counters (phase: one per query; chunks: one per chunk)
     int64_t tbl = 0;     // first entry in the device table
     int maxC = 0;        // most chunks of a query of the bin
     int grid[2] = {0, 0};  // CTAs of the general [0] / D0 [1] kernel
@@ -51,6 +53,7 @@ struct sw_multi {
     const int64_t *off = nullptr;
     const int32_t *order = nullptr;
     int64_t n = 0;
+    int64_t total = 0;   // residues of the database
     int64_t max_len = 0;
     std::vector<int64_t> len_desc;  // sequence lengths in the order's order (longest first)
     std::vector<MultiBin> bins;
@@ -64,6 +67,9 @@ struct sw_multi {
     uint32_t *d_bnd = nullptr;
     uint32_t *d_bnd32 = nullptr;
     int64_t bnd_stride = 0, bnd32_stride = 0;
+    int2 *d_rows = nullptr;       // chunk-phase boundary rows (one per residue)
+    int32_t *d_done = nullptr;    // last phase each sequence of the order finished
+    int32_t *d_status = nullptr;  // set by a bounded wait that gave up
 };
 
 extern "C" {
@@ -141,14 +147,18 @@ int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries, const 
             b->phase = phase;
         }
         b->nq++;
+        b->chunks += p->plan.C;
         b->maxC = std::max(b->maxC, p->plan.C);
     }
     int64_t pos = 0;
     for (auto &b : m->bins) {
+        // several chunks: the (query, chunk) phase walk, or the fused-chunk
+        // tiles when the caller asked for a tile shape
+        b.kind = b.phase ? MULTI_PHASE : items_per_group ? MULTI_FUSED : MULTI_CHUNKS;
         b.tbl = pos;
         pos += b.nq;
         b.cnt = m->n_counters;
-        m->n_counters += b.phase ? b.nq : 1;
+        m->n_counters += b.kind == MULTI_PHASE ? b.nq : b.kind == MULTI_CHUNKS ? b.chunks : 1;
     }
     m->n_counters += 3;  // the int32 launches
     table.resize((size_t)pos);
@@ -221,6 +231,7 @@ int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries, const 
             m->len_desc[(size_t)i] = off[(size_t)k + 1] - off[(size_t)k];
         }
         m->max_len = m->len_desc[0];
+        m->total = off[(size_t)m->n];
         if (m->max_len < 0 || m->len_desc.back() < 0) {
             delete m;
             return api_fail(SW_ERR_INVALID, "db_offsets must be non-decreasing");
@@ -232,13 +243,13 @@ int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries, const 
     int64_t bnd_words = 0, bnd32_words = 0;
     for (auto &b : m->bins) {
         for (int d0 = 0; d0 < 2; ++d0) {
-            const int per_sm = multi_split_blocks_per_sm(b.VL, b.S, b.phase, d0 == 1, m->A);
+            const int per_sm = multi_split_blocks_per_sm(b.VL, b.S, b.kind, d0 == 1, m->A);
             if (per_sm <= 0) {
                 delete m;
                 return api_fail(SW_ERR_INVALID, "no batched kernel for a profile's layout");
             }
             b.grid[d0] = sms * per_sm;
-            if (b.maxC > 1)  // int2 per column
+            if (b.kind == MULTI_FUSED && b.maxC > 1)  // int2 per column
                 bnd_words = std::max(bnd_words, (int64_t)b.grid[d0] * multi_groups_per_cta(b.VL) * m->max_len * 2);
         }
     }
@@ -264,7 +275,14 @@ int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries, const 
     const size_t sz_bnd = up(sizeof(uint32_t) * (size_t)bnd_words);
     const size_t sz_bnd32 = up(sizeof(uint32_t) * (size_t)bnd32_words);
     const size_t sz_order = up(sizeof(int32_t) * (size_t)std::max<int64_t>(m->n, 1));
-    err = cudaMalloc(&m->block, sz_tab + sz_cnt + sz_bnd + sz_bnd32 + sz_order);
+    bool chunk_walk = false;
+    for (const auto &b : m->bins)
+        chunk_walk |= b.kind == MULTI_CHUNKS;
+    // the chunk-phase walk: boundary rows of every residue and a mark per sequence
+    const size_t sz_rows = chunk_walk ? up(sizeof(int2) * (size_t)m->total + 16) : 0;
+    const size_t sz_done = chunk_walk ? up(sizeof(int32_t) * (size_t)m->n) : 0;
+    const size_t sz_status = up(sizeof(int32_t));
+    err = cudaMalloc(&m->block, sz_tab + sz_cnt + sz_bnd + sz_bnd32 + sz_order + sz_rows + sz_done + sz_status);
     if (err != cudaSuccess) {
         m->block = nullptr;
         delete m;
@@ -277,18 +295,21 @@ int sw_multi_create(const sw_profile *const *profiles, int32_t n_queries, const 
     m->d_bnd32 = bnd32_words ? (uint32_t *)(base + sz_tab + sz_cnt + sz_bnd) : nullptr;
     int32_t *d_order = (int32_t *)(base + sz_tab + sz_cnt + sz_bnd + sz_bnd32);
     m->order = d_order;
-    if (!table.empty() || m->n > 0) {
-        if (!table.empty())
-            err = cudaMemcpyAsync(m->d_tables, table.data(), sizeof(MultiQuery) * table.size(),
-                                  cudaMemcpyHostToDevice, st);
-        if (err == cudaSuccess && m->n > 0)
-            err = cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, st);
-        if (err == cudaSuccess)
-            err = cudaStreamSynchronize(st);  // the host copies go out of scope
-        if (err != cudaSuccess) {
-            sw_multi_free(m);
-            return api_cuda_fail((int)err, "sw_multi_create upload");
-        }
+    char *tail = base + sz_tab + sz_cnt + sz_bnd + sz_bnd32 + sz_order;
+    m->d_rows = chunk_walk ? (int2 *)tail : nullptr;
+    m->d_done = chunk_walk ? (int32_t *)(tail + sz_rows) : nullptr;
+    m->d_status = (int32_t *)(tail + sz_rows + sz_done);
+    err = cudaMemsetAsync(m->d_status, 0, sizeof(int32_t), st);
+    if (err == cudaSuccess && !table.empty())
+        err = cudaMemcpyAsync(m->d_tables, table.data(), sizeof(MultiQuery) * table.size(), cudaMemcpyHostToDevice,
+                              st);
+    if (err == cudaSuccess && m->n > 0)
+        err = cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(st);  // the host copies go out of scope
+    if (err != cudaSuccess) {
+        sw_multi_free(m);
+        return api_cuda_fail((int)err, "sw_multi_create upload");
     }
     *out = m;
     return SW_OK;
@@ -305,6 +326,23 @@ int sw_multi_free(sw_multi *m)
     }
     delete m;
     return err == cudaSuccess ? SW_OK : swg::api_cuda_fail((int)err, "sw_multi_free");
+}
+
+int sw_multi_status(const sw_multi *m, int32_t *status_out, void *cuda_stream)
+{
+    if (!m || !status_out)
+        return swg::api_fail(SW_ERR_INVALID, "batch handle or status_out is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int32_t v = 0;
+    cudaError_t err = cudaMemcpyAsync(&v, m->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(m->d_status, 0, sizeof(int32_t), st);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess)
+        return swg::api_cuda_fail((int)err, "sw_multi_status");
+    *status_out = v;
+    return SW_OK;
 }
 
 int sw_align_multi(const sw_multi *m, int32_t gap_open, int32_t gap_extend, int32_t *scores_out, int64_t row_stride,
@@ -341,9 +379,10 @@ int sw_align_multi(const sw_multi *m, int32_t gap_open, int32_t gap_extend, int3
             return api_fail(SW_ERR_RANGE, "gap costs too large for the packed lanes of the batched launch; "
                                           "align these queries one by one");
     }
-    // pairs with min(m, n) >= skip_len could reach the packed lanes'
+    // only pairs with min(m, n) >= skip_len can reach the packed lanes'
     // rescore threshold (score <= max(M) * min(m, n)): the int32 launch
-    // takes them, over the prefix of the length order whose bins reach it
+    // walks them, the prefix of the length order, and rescores the ones
+    // whose packed score reached the threshold
     const int32_t thresh = api_flag_threshold(SW_LANE_I16X2Q, gap_open, m->maxM);
     const int32_t skip_len = m->maxM > 0 ? (int32_t)((thresh + m->maxM - 1) / m->maxM) : INT32_MAX;
     if (m->qlen_no_i32 >= skip_len)  // cannot happen for matrix entries <= 127: skip_len >= 224 > 128
@@ -373,9 +412,13 @@ int sw_align_multi(const sw_multi *m, int32_t gap_open, int32_t gap_extend, int3
     a.off = m->off;
     a.order = m->order;
     a.skip_len = skip_len;
+    a.flag_thresh = thresh;
     a.k_items = m->k_items;
     a.scores = scores_out;
     a.row_stride = row_stride;  // MultiQuery.row is the query's index
+    a.rows = m->d_rows;
+    a.done = m->d_done;
+    a.status = m->d_status;
     const bool d0 = m->minM >= -gap_open;
     for (size_t k = 0; k < m->bins.size(); ++k) {
         const MultiBin &b = m->bins[k];
@@ -383,9 +426,16 @@ int sw_align_multi(const sw_multi *m, int32_t gap_open, int32_t gap_extend, int3
         a.n_queries = b.nq;
         a.n_items = m->n;
         a.counter = m->d_counters + b.cnt;
-        a.bnd = b.maxC > 1 ? m->d_bnd : nullptr;
+        a.bnd = b.kind == MULTI_FUSED && b.maxC > 1 ? m->d_bnd : nullptr;
         a.bnd_stride = m->bnd_stride;
-        const int kr = launch_multi_split(b.VL, b.S, b.phase, a, b.grid[d0 ? 1 : 0], st);
+        if (b.kind == MULTI_CHUNKS) {
+            // every sequence starts before the bin's first phase (marks of
+            // an earlier bin's walk would skip its waits)
+            err = cudaMemsetAsync(m->d_done, 0xff, sizeof(int32_t) * (size_t)m->n, st);
+            if (err != cudaSuccess)
+                return api_cuda_fail((int)err, "cudaMemsetAsync(marks)");
+        }
+        const int kr = launch_multi_split(b.VL, b.S, b.kind, a, b.grid[d0 ? 1 : 0], st);
         if (kr)
             return api_cuda_fail(kr, "batched kernel launch");
     }

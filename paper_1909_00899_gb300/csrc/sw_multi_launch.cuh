@@ -5,10 +5,14 @@
 
 namespace swg {
 
-template <int L, int S, bool D0, bool AC, bool PHASE>
+// KIND: MULTI_FUSED (tiles, all chunks of a unit in one CTA), MULTI_PHASE
+// (single-chunk queries), MULTI_CHUNKS (the (query, chunk) phase walk)
+template <int L, int S, bool D0, bool AC, int KIND>
 int multi_split_inst(const MultiArgs *a, int grid, cudaStream_t st, int *per_sm, int A)
 {
-    auto kern = PHASE ? sw_multi_phase_kernel<L, S, D0, AC> : sw_multi_split_kernel<L, S, D0, AC>;
+    auto kern = KIND == MULTI_PHASE    ? sw_multi_phase_kernel<L, S, D0, AC>
+                : KIND == MULTI_CHUNKS ? sw_multi_chunks_kernel<L, S, D0, AC>
+                                       : sw_multi_split_kernel<L, S, D0, AC>;
     constexpr size_t kMaxSmem = (size_t)34 * L * SegPad<S, 4>::value * 4;
     static SmemAttrOnce attr;
     const int attr_err = set_smem_attr_once(attr, kern, kMaxSmem);
@@ -48,10 +52,10 @@ int multi_i32_inst(const MultiArgs *a, int grid, cudaStream_t st, int *per_sm, i
 // One translation unit's split layouts: VL virtual lanes (L = VL / 2
 // threads) x S positions, the always-corrected pass where the per-query
 // kernels run it (split_ac), the general pass when some score is below -o.
-// PHASE: the phase kernel of single-chunk queries, else the fused-chunk one
-#define SWG_MULTI_CASE(VL, SS)                                                                            \
-    if (VL_ == VL && S_ == SS)                                                                            \
-        return d0 ? multi_split_inst<VL / 2, SS, true, split_ac(VL, SS), PHASE>(a, grid, st, per_sm, A) \
-                  : multi_split_inst<VL / 2, SS, false, false, PHASE>(a, grid, st, per_sm, A);
+// KIND: the kernel kind of the translation unit
+#define SWG_MULTI_CASE(VL, SS)                                                                           \
+    if (VL_ == VL && S_ == SS)                                                                           \
+        return d0 ? multi_split_inst<VL / 2, SS, true, split_ac(VL, SS), KIND>(a, grid, st, per_sm, A) \
+                  : multi_split_inst<VL / 2, SS, false, false, KIND>(a, grid, st, per_sm, A);
 
 }  // namespace swg

@@ -34,7 +34,8 @@ EXPORTS = (
     "sw_probe_cell_rate", "sw_probe_cell_rate_pass", "sw_version", "sw_db_create", "sw_db_free", "sw_align_db",
     "sw_align_db_ends", "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats",
     "sw_align_batch_noalloc", "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends",
-    "sw_align_lazyf_pairs_lane", "sw_multi_create", "sw_align_multi", "sw_multi_free", "sw_mem_available",
+    "sw_align_lazyf_pairs_lane", "sw_multi_create", "sw_align_multi", "sw_multi_free", "sw_multi_status",
+    "sw_mem_available",
 )
 
 
@@ -103,6 +104,8 @@ def lib():
         L.sw_align_multi.argtypes = [_vp, _i32, _i32, _vp, _i64, _vp]
         L.sw_multi_free.restype = ctypes.c_int
         L.sw_multi_free.argtypes = [_vp]
+        L.sw_multi_status.restype = ctypes.c_int
+        L.sw_multi_status.argtypes = [_vp, ctypes.POINTER(_i32), _vp]
         L.sw_mem_available.restype = ctypes.c_int
         L.sw_mem_available.argtypes = [ctypes.POINTER(_i64)]
         L.sw_stream_sync.restype = ctypes.c_int
@@ -417,6 +420,14 @@ def sw_multi_create(profiles, db, items_per_group=0, stream=None):
 
 def sw_multi_free(batch):
     batch.free()
+
+
+def sw_multi_status(batch, stream=None):
+    """The batch's status word (then cleared): 0, or 1 when a bounded wait
+    of the chunk-phase walk gave up since the last read."""
+    out = _i32(0)
+    _check(lib().sw_multi_status(batch.handle, ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def sw_align_multi(batch, gap_open, gap_extend, scores_out, stream=None):

@@ -157,7 +157,7 @@ def test_graph_captured_ragged_batch(sw, small_db):
         ba.free()
 
 
-def _multi_case(sw, M, o, e, seqs, queries, layouts):
+def _multi_case(sw, M, o, e, seqs, queries, layouts, items_per_group=0):
     """sw_align_multi on a padded score matrix, eagerly and replayed from a
     CUDA graph, every row against the oracle."""
     from helpers import pack_list
@@ -170,11 +170,12 @@ def _multi_case(sw, M, o, e, seqs, queries, layouts):
             profs.append(sw.Profile(q, M))
         else:
             profs.append(sw.Profile(q, M, sw.SW_LANE_I16X2Q, lanes=lay[0], seg_len=lay[1]))
-    batch = sw.Multi(profs, h)
+    batch = sw.Multi(profs, h, items_per_group=items_per_group)
     n = h.n
     out = torch.full((len(queries), n + 5), -7, dtype=torch.int32, device="cuda")  # padded rows
     sw.sw_align_multi(batch, o, e, out)
     torch.cuda.synchronize()
+    assert sw.sw_multi_status(batch) == 0  # no bounded wait gave up
     got = out.cpu().numpy()
     for i, q in enumerate(queries):
         want = oracle.gotoh_batch(q, db, off, M, o, e)
@@ -258,8 +259,11 @@ def test_batched_launch_every_layout_exact(sw):
     seqs.append(np.concatenate([synth.residues(rng, 30, 20), long_q[1000:5200], synth.residues(rng, 20, 20)]))
     seqs.append(np.concatenate([queries[-2][100:2650], synth.residues(rng, 400, 20)]))
     got, db, off = _multi_case(sw, M, 11, 1, seqs, queries, lays)
-    assert got[-1, -2] > 28543  # scored by the int32 launch
+    assert got[-1, -2] > 32767  # overflowed the packed lanes, rescored by the int32 launch
     assert got[-2, -1] > 2550 * 4
+    # the fused-chunk tiles (items_per_group > 0) on the multi-chunk queries
+    got2, _, _ = _multi_case(sw, M, 11, 1, seqs, queries, lays, items_per_group=3)
+    np.testing.assert_array_equal(got2, got)
 
 
 def test_batched_launch_general_pass_and_dna(sw):
