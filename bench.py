@@ -1025,7 +1025,8 @@ def ragged_summary(args, n_queries):
             "autotune": table.to_json(), "clocks": clocks, "check": {"queries_checked": 8, "db_sample": 300},
             "mode": "batched" if ba.multi is not None else "per_query",
             "launches_per_replay": (len(layouts) + n_i32) if ba.multi is not None else None,
-            "launch_bins": [{"lanes": x[0], "seg_len": x[1], "kernel": "phase" if x[2] else "fused-chunk"}
+            "launch_bins": [{"lanes": x[0], "seg_len": x[1],
+                             "kernel": "phase" if x[2] else "fused-chunk" if ba.items_per_group else "chunk-walk"}
                             for x in layouts]}
     ba.free()
     return line

@@ -349,9 +349,18 @@ int sw_align_multi(const sw_multi *batch, int32_t gap_open, int32_t gap_extend,
 int sw_multi_free(sw_multi *batch);
 /* The batch handle's status word, then cleared: 0, or 1 when a bounded
  * wait of the (query, chunk) phase walk gave up (about a second) since the
- * last read, in which case some scores of those calls may be wrong.
- * Synchronises cuda_stream. */
+ * last read, in which case some scores of those calls may be wrong.  Once
+ * the word is set, later waits give up at their first poll until it is
+ * read, so a launch that lost a mark still ends.  Synchronises cuda_stream. */
 int sw_multi_status(const sw_multi *batch, int32_t *status_out, void *cuda_stream);
+/* The bound of the phase walk's waits for the handle's later calls:
+ * max_polls polls of about 256 ns (0: the default, 2^22, about a second).
+ * unreachable != 0 is for testing the bound: every wait then awaits a mark
+ * no phase writes, runs out and sets the status word; the scores of such
+ * calls are undefined (but every access stays inside the handle's buffers
+ * and the caller's score matrix).  SW_ERR_INVALID for a NULL handle or
+ * max_polls < 0.  Host only, no CUDA call. */
+int sw_multi_set_wait(sw_multi *batch, int32_t max_polls, int32_t unreachable);
 
 /*
  * sw_align_batch_noalloc — sw_align_batch (same arguments, results and

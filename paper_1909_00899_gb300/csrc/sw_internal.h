@@ -209,6 +209,8 @@ struct MultiArgs {
     int2 *rows;
     int32_t *done;
     int32_t *status;
+    int32_t wait_limit;     // polls (about 256 ns each) before a wait gives up
+    int32_t wait_skew;      // added to the awaited mark: 0, or past every phase (a test of the bound)
 };
 
 // multi-query launchers (sw_k_multi*.cu): split s16x2 layouts (virtual lanes

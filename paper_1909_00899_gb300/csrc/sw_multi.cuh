@@ -219,8 +219,27 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
 // CTA (this CTA's warps finished theirs at the phase barrier), and as both
 // phases run longest first, P reaches a sequence long after P - 1 finished
 // it: the wait is a formality with no cycle.  It is bounded all the same
-// (about a second), after which the group sets the status word and goes on.
-constexpr int MULTI_WAIT_LIMIT = 1 << 22;  // polls of about 256 ns
+// (p.wait_limit polls of about 256 ns, a second by default), after which the
+// group sets the status word and goes on; once the word is set, later waits
+// give up at their first poll, so a launch that lost a mark still ends in
+// about a second.
+
+// waits (acquire) until *mark >= need, at most `limit` polls; sets the
+// status word when it gives up, and gives up at once when the word is set.
+// Kept out of line: inlined, it changed the register allocation of the
+// kernel's cell loop (more spills on the 64 x 40 layout).
+static __device__ __noinline__ void multi_wait_mark(int32_t *mark, int need, int limit, int32_t *status)
+{
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device> d(*mark);
+    int it = 0;
+    while (d.load(cuda::memory_order_acquire) < need) {
+        if (++it > limit || *reinterpret_cast<volatile int32_t *>(status) != 0) {
+            atomicExch(status, 1);
+            return;
+        }
+        __nanosleep(256);
+    }
+}
 
 template <int L, int S, bool D0, bool AC>
 __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC>::value)
@@ -296,15 +315,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
                 const int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
                 // wait until this sequence is done with the previous phase
                 if (w < p.n_items && phase > 0 && gl == 0) {
-                    cuda::atomic_ref<int32_t, cuda::thread_scope_device> d(p.done[w]);
-                    int it = 0;
-                    while (d.load(cuda::memory_order_acquire) < phase - 1) {
-                        if (++it > MULTI_WAIT_LIMIT) {
-                            atomicExch(p.status, 1);
-                            break;
-                        }
-                        __nanosleep(256);
-                    }
+                    multi_wait_mark(p.done + w, phase - 1 + p.wait_skew, p.wait_limit, p.status);
                 }
                 if (gl == 0) {
                     s_w[gslot] = w < p.n_items ? w : -1;

@@ -44,6 +44,8 @@ struct MultiI32 {
 // sequences per lane group per unit when the caller leaves it to the library
 // (the rate on GB300 rose from 1 to 4; the autotuner can pick per batch)
 constexpr int32_t kDefaultItems = 4;
+// polls of about 256 ns before a wait of the chunk walk gives up (a second)
+constexpr int32_t kDefaultWaitPolls = 1 << 22;
 
 struct sw_multi {
     int device = 0;
@@ -70,6 +72,8 @@ struct sw_multi {
     int2 *d_rows = nullptr;       // chunk-phase boundary rows (one per residue)
     int32_t *d_done = nullptr;    // last phase each sequence of the order finished
     int32_t *d_status = nullptr;  // set by a bounded wait that gave up
+    int32_t wait_limit = kDefaultWaitPolls;
+    int32_t wait_skew = 0;
 };
 
 extern "C" {
@@ -345,6 +349,19 @@ int sw_multi_status(const sw_multi *m, int32_t *status_out, void *cuda_stream)
     return SW_OK;
 }
 
+int sw_multi_set_wait(sw_multi *m, int32_t max_polls, int32_t unreachable)
+{
+    if (!m)
+        return swg::api_fail(SW_ERR_INVALID, "batch handle is NULL");
+    if (max_polls < 0)
+        return swg::api_fail(SW_ERR_INVALID, "max_polls must be >= 0");
+    m->wait_limit = max_polls ? max_polls : kDefaultWaitPolls;
+    // past every phase number a walk reaches (phases < 2^30 by the chunk and
+    // query counts the handle accepts)
+    m->wait_skew = unreachable ? (1 << 30) : 0;
+    return SW_OK;
+}
+
 int sw_align_multi(const sw_multi *m, int32_t gap_open, int32_t gap_extend, int32_t *scores_out, int64_t row_stride,
                    void *cuda_stream)
 {
@@ -419,6 +436,8 @@ int sw_align_multi(const sw_multi *m, int32_t gap_open, int32_t gap_extend, int3
     a.rows = m->d_rows;
     a.done = m->d_done;
     a.status = m->d_status;
+    a.wait_limit = m->wait_limit;
+    a.wait_skew = m->wait_skew;
     const bool d0 = m->minM >= -gap_open;
     for (size_t k = 0; k < m->bins.size(); ++k) {
         const MultiBin &b = m->bins[k];

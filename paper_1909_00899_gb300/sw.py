@@ -35,7 +35,7 @@ EXPORTS = (
     "sw_align_db_ends", "sw_align_lazyf_db", "sw_align_lazyf_pairs", "sw_align_lazyf_db_stats",
     "sw_align_batch_noalloc", "sw_align_batch_ends", "sw_plan_query", "sw_align_pairs_ends",
     "sw_align_lazyf_pairs_lane", "sw_multi_create", "sw_align_multi", "sw_multi_free", "sw_multi_status",
-    "sw_mem_available",
+    "sw_multi_set_wait", "sw_mem_available",
 )
 
 
@@ -106,6 +106,8 @@ def lib():
         L.sw_multi_free.argtypes = [_vp]
         L.sw_multi_status.restype = ctypes.c_int
         L.sw_multi_status.argtypes = [_vp, ctypes.POINTER(_i32), _vp]
+        L.sw_multi_set_wait.restype = ctypes.c_int
+        L.sw_multi_set_wait.argtypes = [_vp, _i32, _i32]
         L.sw_mem_available.restype = ctypes.c_int
         L.sw_mem_available.argtypes = [ctypes.POINTER(_i64)]
         L.sw_stream_sync.restype = ctypes.c_int
@@ -428,6 +430,13 @@ def sw_multi_status(batch, stream=None):
     out = _i32(0)
     _check(lib().sw_multi_status(batch.handle, ctypes.byref(out), _stream(stream)))
     return int(out.value)
+
+
+def sw_multi_set_wait(batch, max_polls=0, unreachable=False):
+    """Bound of the chunk-phase walk's waits (polls of about 256 ns; 0: the
+    default, about a second); unreachable=True makes every wait run out
+    (a test of the bound: the status word is set, the scores undefined)."""
+    _check(lib().sw_multi_set_wait(batch.handle, int(max_polls), 1 if unreachable else 0))
 
 
 def sw_align_multi(batch, gap_open, gap_extend, scores_out, stream=None):

@@ -68,6 +68,11 @@ def test_invalid_arguments_rejected_without_cuda(swlib):
     assert "s16x2" in swlib.sw_last_error()
     assert L.sw_probe_cell_rate_pass(3, 1, 10, ctypes.byref(cps), None) == swlib.SW_ERR_INVALID
     assert "s8x4" in swlib.sw_last_error()
+    # batched-launch handle calls: NULL handle
+    assert L.sw_multi_set_wait(None, 0, 0) == swlib.SW_ERR_INVALID
+    st = ctypes.c_int32(0)
+    assert L.sw_multi_status(None, ctypes.byref(st), None) == swlib.SW_ERR_INVALID
+    assert L.sw_align_multi(None, 11, 1, None, 0, None) == swlib.SW_ERR_INVALID
 
 
 def test_plan_query_covers_the_query_host_only(swlib):

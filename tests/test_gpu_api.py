@@ -2,6 +2,8 @@
 graph-captured many-query batch, the autotuner, the serving loop and the
 bounded stream wait.  Every score is compared bit-exactly with the oracle
 (or with a path already compared with it)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -279,6 +281,37 @@ def test_batched_launch_general_pass_and_dna(sw):
     for o, e, mm in ((6, 1, -4), (3, 1, -5), (5, 5, -2)):
         M = synth.dna_matrix(match=2, mismatch=mm)
         _multi_case(sw, M, o, e, refs, queries, [None] * len(queries))
+
+
+def test_batched_launch_wait_bound_sets_status(sw, small_db):
+    """The chunk walk's bounded wait: with every wait made to await a mark
+    no phase writes, each runs out, the status word reads 1 (then clears),
+    the launch ends and the context stays usable; with the bound restored
+    the next call on the same handle is exact and reads 0."""
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    q = synth.residues(np.random.default_rng(2014), 700, 20)
+    p = sw.Profile(q, M, sw.SW_LANE_I16X2Q, lanes=16, seg_len=8)  # 128 positions a chunk: 6 chunks
+    assert p.plan()["chunks"] > 1
+    batch = sw.Multi([p], h)
+    out = torch.full((1, h.n), -1, dtype=torch.int32, device="cuda")
+    sw.sw_multi_set_wait(batch, 64, unreachable=True)
+    t0 = time.time()
+    sw.sw_align_multi(batch, 11, 1, out)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30
+    assert sw.sw_multi_status(batch) == 1
+    assert sw.sw_multi_status(batch) == 0  # read clears it
+    sw.sw_multi_set_wait(batch, 0)
+    out.fill_(-1)
+    sw.sw_align_multi(batch, 11, 1, out)
+    torch.cuda.synchronize()
+    assert sw.sw_multi_status(batch) == 0
+    np.testing.assert_array_equal(out.cpu().numpy()[0], oracle.gotoh_batch(q, db, off, M, 11, 1))
+    batch.free()
+    p.free()
+    h.free()
 
 
 def test_batched_launch_rejects_what_it_cannot_run(sw, small_db):
