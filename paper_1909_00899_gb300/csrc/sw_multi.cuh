@@ -241,6 +241,10 @@ static __device__ __noinline__ void multi_wait_mark(int32_t *mark, int need, int
     }
 }
 
+// reads a CTA-uniform value parked in shared memory afresh at each use, so
+// that it holds no register across the cell loop
+__device__ __forceinline__ int multi_uniform(const int &v) { return *reinterpret_cast<const volatile int *>(&v); }
+
 template <int L, int S, bool D0, bool AC>
 __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC>::value)
     sw_multi_chunks_kernel(const MultiArgs p)
@@ -250,10 +254,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
     constexpr int QH = L * S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *sprof = reinterpret_cast<uint32_t *>(smem_raw);
-    __shared__ int s_skip;
-    // the phase's query, kept in shared memory: the cell loop needs every
-    // register (the S = 40 layouts spilled with it in registers)
+    // the walk's state and the phase's query, kept in shared memory: the
+    // cell loop needs every register (the S = 40 layouts spilled with the
+    // query in registers, and loop state held across it costs moves)
     __shared__ MultiQuery s_q;
+    __shared__ int s_phase, s_chunk, s_nchunks, s_query;
     // each group's item and sequence, parked over the cell loop
     __shared__ long long s_w[(BATCH_THREADS / 32) * G];
     __shared__ int s_seq[(BATCH_THREADS / 32) * G];
@@ -261,88 +266,114 @@ __global__ void __launch_bounds__(BATCH_THREADS, SplitMinBlocks<S, D0, false, AC
     const int gl = lane & (L - 1);
     const int grp = lane / L;
     const int gslot = (int)(threadIdx.x >> 5) * G + grp;
-    const int pb = split_pb<D0>(p.o);
-    const int total = (p.A + 2) * L * SP;
-    int phase = 0;  // running (query, chunk) phase number
-    for (int qi = 0; qi < p.n_queries; ++qi) {
-        __syncthreads();  // every thread is done with the previous query's record
-        if (threadIdx.x == 0)
-            s_q = p.queries[qi];
-        __syncthreads();
-        const int nchunks = s_q.C;
-        for (int c = 0; c < nchunks; ++c, ++phase) {
-            __syncthreads();  // every warp is done with the previous phase's profile
-            if (threadIdx.x == 0)
-                s_skip = *reinterpret_cast<volatile unsigned long long *>(p.counter + phase) >=
-                         (unsigned long long)p.n_items;
-            __syncthreads();
-            if (s_skip)
-                continue;  // its sequences are all taken
-            // stage chunk c: virtual lanes l and L + l paired in one word;
-            // row A: an unknown residue (the smallest entry), row A+1: inert
-            {
-                const int8_t *gprof = s_q.prof + (size_t)c * p.A * 2 * QH;
-                const int qbase = c * 2 * QH;
-                const int qlen = s_q.qlen;
-                for (int idx = threadIdx.x; idx < total; idx += BATCH_THREADS) {
-                    const int a = idx / (L * SP);
-                    const int rem = idx - a * (L * SP);
-                    const int l = rem / SP;
-                    const int j = rem - l * SP;
-                    int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
-                    if (a <= p.A && j < S) {
-                        const int plo = l * S + j, phi = QH + l * S + j;
-                        if (qbase + plo < qlen)
-                            lo = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + plo] : (int)p.min_m) + pb;
-                        if (qbase + phi < qlen)
-                            hi = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + phi] : (int)p.min_m) + pb;
-                    }
-                    sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] =
-                        (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
-                }
-            }
-            __syncthreads();
+    if (threadIdx.x == 0) {
+        s_phase = -1;  // before the first phase: chunk -1 of a query of no chunks
+        s_chunk = -1;
+        s_nchunks = 0;
+        s_query = -1;
+    }
+    for (;;) {
+        __syncthreads();  // every warp is done with the previous phase's profile and record
+        if (threadIdx.x == 0) {
+            // the next phase whose sequences are not all taken
+            int ph = s_phase, c = s_chunk, nc = s_nchunks, qi = s_query;
             for (;;) {
-                unsigned long long ubase = 0;
-                if (lane == 0)
-                    ubase = atomicAdd(p.counter + phase, (unsigned long long)G);
-                ubase = __shfl_sync(MULTI_FULL, ubase, 0);
-                if ((int64_t)ubase >= p.n_items)
+                ++ph;
+                if (++c >= nc) {
+                    c = 0;
+                    if (++qi >= p.n_queries)
+                        break;
+                    s_q = p.queries[qi];
+                    nc = s_q.C;
+                    if (nc < 1) {
+                        --ph;  // a query of no chunks has no phase
+                        c = -1;
+                        nc = 0;
+                        continue;
+                    }
+                }
+                if (*reinterpret_cast<volatile unsigned long long *>(p.counter + ph) < (unsigned long long)p.n_items)
                     break;
-                const int64_t w = (int64_t)ubase + grp;
-                const int seq = w < p.n_items ? p.order[w] : -1;
-                const int64_t start = seq >= 0 ? p.off[seq] : 0;
-                const int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
-                // wait until this sequence is done with the previous phase
-                if (w < p.n_items && phase > 0 && gl == 0) {
-                    multi_wait_mark(p.done + w, phase - 1 + p.wait_skew, p.wait_limit, p.status);
+            }
+            s_phase = ph;
+            s_chunk = c;
+            s_nchunks = nc;
+            s_query = qi;
+        }
+        __syncthreads();
+        if (s_query >= p.n_queries)
+            break;
+        // stage chunk c: virtual lanes l and L + l paired in one word;
+        // row A: an unknown residue (the smallest entry), row A+1: inert
+        {
+            const int c = s_chunk;
+            const int pb = split_pb<D0>(p.o);
+            const int total = (p.A + 2) * L * SP;
+            const int8_t *gprof = s_q.prof + (size_t)c * p.A * 2 * QH;
+            const int qbase = c * 2 * QH;
+            const int qlen = s_q.qlen;
+            for (int idx = threadIdx.x; idx < total; idx += BATCH_THREADS) {
+                const int a = idx / (L * SP);
+                const int rem = idx - a * (L * SP);
+                const int l = rem / SP;
+                const int j = rem - l * SP;
+                int lo = LaneQ16::PAD, hi = LaneQ16::PAD;
+                if (a <= p.A && j < S) {
+                    const int plo = l * S + j, phi = QH + l * S + j;
+                    if (qbase + plo < qlen)
+                        lo = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + plo] : (int)p.min_m) + pb;
+                    if (qbase + phi < qlen)
+                        hi = (a < p.A ? (int)gprof[(size_t)a * 2 * QH + phi] : (int)p.min_m) + pb;
                 }
-                if (gl == 0) {
-                    s_w[gslot] = w < p.n_items ? w : -1;
-                    s_seq[gslot] = seq;
+                sprof[((a * (SP / 4) + j / 4) * L + l) * 4 + (j % 4)] =
+                    (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+            }
+        }
+        __syncthreads();
+        const bool has_prev = s_chunk > 0, has_next = s_chunk + 1 < s_nchunks;
+        for (;;) {
+            const int phase = multi_uniform(s_phase);
+            unsigned long long ubase = 0;
+            if (lane == 0)
+                ubase = atomicAdd(p.counter + phase, (unsigned long long)G);
+            ubase = __shfl_sync(MULTI_FULL, ubase, 0);
+            if ((int64_t)ubase >= p.n_items)
+                break;
+            const int64_t w = (int64_t)ubase + grp;
+            const int seq = w < p.n_items ? p.order[w] : -1;
+            const int64_t start = seq >= 0 ? p.off[seq] : 0;
+            const int len = seq >= 0 ? (int)(p.off[seq + 1] - start) : 0;
+            // wait until this sequence is done with the previous phase
+            if (w < p.n_items && phase > 0 && gl == 0)
+                multi_wait_mark(p.done + w, phase - 1 + p.wait_skew, p.wait_limit, p.status);
+            if (gl == 0) {
+                s_w[gslot] = w < p.n_items ? w : -1;
+                s_seq[gslot] = seq;
+            }
+            __syncwarp(MULTI_FULL);
+            const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
+            const uint32_t mx = split_unit<L, S, D0, false, false, AC>(sprof, p.db, start, len, ncols, p.A, p.o, p.e,
+                                                                       p.one, has_prev, has_next, p.rows, gl);
+            __syncwarp(MULTI_FULL);  // the group's boundary-row stores come before the mark
+            if (gl == 0) {
+                const long long wi = s_w[gslot];
+                const int sq = s_seq[gslot];
+                const int c2 = multi_uniform(s_chunk);
+                if (sq >= 0) {
+                    // the maximum over the chunks so far (chunk c - 1 wrote
+                    // before it published its mark); h-space bias BX + pb - o
+                    const int sc = max((int)(int16_t)(mx & 0xffffu), (int)(int16_t)(mx >> 16)) -
+                                   (LaneQ16::BX + split_pb<D0>(p.o) - p.o);
+                    int32_t *dst = p.scores + s_q.row * p.row_stride + sq;
+                    *dst = c2 > 0 ? max(sc, *dst) : sc;
                 }
-                __syncwarp(MULTI_FULL);
-                const int ncols = (int)__reduce_max_sync(MULTI_FULL, (unsigned)len);
-                const uint32_t mx = split_unit<L, S, D0, false, false, AC>(sprof, p.db, start, len, ncols, p.A, p.o,
-                                                                           p.e, p.one, c > 0, c + 1 < nchunks,
-                                                                           p.rows, gl);
-                __syncwarp(MULTI_FULL);  // the group's boundary-row stores come before the mark
-                if (gl == 0) {
-                    const long long wi = s_w[gslot];
-                    const int sq = s_seq[gslot];
-                    if (sq >= 0) {
-                        // the maximum over the chunks so far (chunk c - 1 wrote
-                        // before it published its mark); h-space bias BX + pb - o
-                        const int sc = max((int)(int16_t)(mx & 0xffffu), (int)(int16_t)(mx >> 16)) -
-                                       (LaneQ16::BX + pb - p.o);
-                        int32_t *dst = p.scores + s_q.row * p.row_stride + sq;
-                        *dst = c > 0 ? max(sc, *dst) : sc;
-                    }
-                    if (wi >= 0) {
-                        __threadfence();
-                        cuda::atomic_ref<int32_t, cuda::thread_scope_device> d(p.done[wi]);
-                        d.store(phase, cuda::memory_order_release);
-                    }
+                if (wi >= 0) {
+                    __threadfence();
+                    cuda::atomic_ref<int32_t, cuda::thread_scope_device> d(p.done[wi]);
+                    // the phase from shared memory again, except on the 32 x 40
+                    // layout, whose register allocation spilled that way (the
+                    // allocation at 128 registers shifts with any change)
+                    d.store((L == 16 && S == 40) ? phase : multi_uniform(s_phase), cuda::memory_order_release);
                 }
             }
         }
