@@ -3,9 +3,10 @@
 Each query's profile is built with the layout the autotuner picked for its
 length (or the built-in automatic one).  When every profile runs on the
 split s16x2 lanes (the automatic lane type), the whole batch is one
-sw_align_multi call -- one persistent launch per layout over every
-(query, tile of database sequences) unit, plus one int32 launch for the
-few pairs that could overflow the packed lanes -- captured once into a
+sw_align_multi call -- one persistent launch per layout bin (single-chunk
+queries walk query by query, longer ones (query, chunk) phase by phase),
+plus one int32 launch that rescores the few pairs whose packed score
+reached the s16 threshold -- captured once into a
 CUDA graph and replayed.  Otherwise every query's sw_align_db call is
 captured instead, spread over side streams.  Scores land in a
 [n_queries, n_db] int32 device matrix.
@@ -34,7 +35,7 @@ class BatchAligner:
         self.stream = stream or torch.cuda.Stream()
         self.side = [torch.cuda.Stream() for _ in range(max(1, streams))]
         self.mode = mode
-        self.items_per_group = int(items_per_group)  # batched tile: sequences per lane group (0: default)
+        self.items_per_group = int(items_per_group)  # > 0: fused-chunk tiles of that many sequences per lane group
         self.graph = None
         self.profiles = []
         self.order = None

@@ -182,8 +182,10 @@ struct MultiQuery {
     int64_t row;           // its score row (the query's index in the batch)
 };
 
-// Parameters of one multi-query launch: every (query, tile) unit of
-// queries[0 .. n_queries) x the first n_items entries of the length order.
+// Parameters of one multi-query launch: every pair of queries[0 ..
+// n_queries) x the first n_items entries of the length order (the phase
+// kernel and the chunk walk pull them query by query, or chunk by chunk;
+// the fused-chunk kernel in (query, tile of sequences) units).
 struct MultiArgs {
     const MultiQuery *queries;
     int32_t n_queries;
@@ -198,8 +200,9 @@ struct MultiArgs {
     int32_t flag_thresh;    // the int32 launch rescores candidates whose packed score reached it
     int32_t *scores;        // row-major [query][row_stride]
     int64_t row_stride;
-    int32_t k_items;        // sequences per lane group per unit (the tile is k_items x groups per CTA)
-    unsigned long long *counter;  // unit counter (phase kernel: one per query), zero at launch
+    int32_t k_items;        // fused-chunk kernel: sequences per lane group per unit (a tile is k_items x groups per CTA)
+    unsigned long long *counter;  // work counters, zero at launch: one per query (phase kernel), one per
+                                  // (query, chunk) phase (chunk walk), one per launch (fused-chunk)
     uint32_t *bnd;          // per-group boundary-row slots (32-bit words), null when C == 1 throughout
     int64_t bnd_stride;     // words per group slot
     // the chunk-phase kernel: boundary rows of every database residue
@@ -214,8 +217,8 @@ struct MultiArgs {
 };
 
 // multi-query launchers (sw_k_multi*.cu): split s16x2 layouts (virtual lanes
-// x segment length; phase: the phase kernel of single-chunk queries, whose
-// counter is one per query, else the fused-chunk kernel) and the int32
+// x segment length; kind: the phase kernel of single-chunk queries, the
+// (query, chunk) walk or the fused-chunk kernel of longer ones) and the int32
 // layouts 32 x {8, 16, 32} of the pairs that could overflow the packed
 // lanes; grid is fixed by the caller (its boundary slots are sized for it).
 constexpr int MULTI_FUSED = 0, MULTI_PHASE = 1, MULTI_CHUNKS = 2;
