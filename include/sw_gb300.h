@@ -304,8 +304,10 @@ int sw_align_lazyf_db_stats(const sw_profile *prof, const sw_db *db,
  * by their layout, reads the database's offsets back once to order its
  * sequences exactly by length, uploads the tables and that order and sizes
  * the per-group boundary slots (it synchronises cuda_stream and allocates
- * about 4 bytes per sequence plus the slots); sw_align_multi then issues a
- * memset and one launch per layout (two when a layout holds both one- and
+ * about 4 bytes per sequence, plus 8 bytes per residue when some query has
+ * several chunks, or the slots of the fused-chunk tiles); sw_align_multi
+ * then issues a few memsets (work counters, the walk's marks) and one
+ * launch per layout (two when a layout holds both one- and
  * several-chunk queries), plus one int32 launch per int32 layout when some
  * pairs could overflow the packed lanes, with no host
  * synchronisation: it can be captured into a CUDA graph.
