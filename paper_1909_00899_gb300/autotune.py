@@ -33,7 +33,7 @@ CANDIDATES = {
     sw.SW_LANE_I32: ((1, 16), (1, 32), (4, 8), (4, 32), (8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12),
                      (32, 16), (16, 32), (32, 32)),
     # split-query s16x2: virtual lanes (two per thread)
-    sw.SW_LANE_I16X2Q: ((2, 16), (2, 32), (16, 8), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32),
+    sw.SW_LANE_I16X2Q: ((2, 16), (2, 32), (16, 8), (16, 32), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32),
                         (32, 40), (64, 8), (64, 16), (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)),
 }
 

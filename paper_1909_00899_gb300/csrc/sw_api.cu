@@ -102,8 +102,8 @@ const Choice kAllI32[] = {{1, 16}, {1, 32}, {4, 8},   {4, 32},  {8, 8},  {8, 16}
                           {16, 16}, {32, 8}, {32, 12}, {32, 16}, {8, 32}, {16, 32}, {32, 32}};
 const Choice kAllI16[] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {32, 8}, {32, 12}, {32, 16}, {16, 32}, {32, 24}, {32, 32}};
 const Choice kAllI8[] = {{8, 16}, {16, 16}, {32, 16}};
-const Choice kAllQ16[] = {{2, 16}, {2, 32}, {16, 8},  {32, 8},  {32, 12}, {32, 16}, {32, 20}, {32, 24}, {32, 32},
-                          {32, 40}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 28}, {64, 32}, {64, 40}};
+const Choice kAllQ16[] = {{2, 16}, {2, 32}, {16, 8},  {16, 32}, {32, 8},  {32, 12}, {32, 16}, {32, 20}, {32, 24},
+                          {32, 32}, {32, 40}, {64, 8}, {64, 16}, {64, 20}, {64, 24}, {64, 28}, {64, 32}, {64, 40}};
 
 bool plan_supported(int lane, int L, int S)
 {
@@ -111,7 +111,7 @@ bool plan_supported(int lane, int L, int S)
                       : lane == SW_LANE_I16X2 ? kAllI16
                       : lane == SW_LANE_I8X4  ? kAllI8
                                               : kAllQ16;
-    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 17);
+    const int n = lane == SW_LANE_I32 ? 14 : (lane == SW_LANE_I16X2 ? 10 : lane == SW_LANE_I8X4 ? 3 : 18);
     for (int i = 0; i < n; ++i)
         if (t[i].L == L && t[i].S == S)
             return true;
@@ -138,7 +138,8 @@ struct AutoChoice {
     double gcups;
 };
 const AutoChoice kAuto[] = {
-    {SW_LANE_I16X2Q, 16, 8, 2894},  {SW_LANE_I16X2Q, 32, 8, 4290},  {SW_LANE_I16X2Q, 32, 16, 4340},
+    {SW_LANE_I16X2Q, 16, 8, 2894},  {SW_LANE_I16X2Q, 16, 32, 4491}, {SW_LANE_I16X2Q, 32, 8, 4290},
+    {SW_LANE_I16X2Q, 32, 16, 4340},
     {SW_LANE_I16X2Q, 32, 12, 4157}, {SW_LANE_I16X2Q, 32, 20, 4680}, {SW_LANE_I16X2Q, 32, 24, 5109},
     {SW_LANE_I16X2Q, 32, 32, 5127}, {SW_LANE_I16X2Q, 32, 40, 5523}, {SW_LANE_I16X2Q, 64, 8, 4388},
     {SW_LANE_I16X2Q, 64, 16, 4932}, {SW_LANE_I16X2Q, 64, 20, 5110}, {SW_LANE_I16X2Q, 64, 24, 5340},

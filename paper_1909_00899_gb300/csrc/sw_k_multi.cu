@@ -9,6 +9,7 @@ int multi_split_narrow(int VL_, int S_, bool d0, const MultiArgs *a, int grid, c
 {
     constexpr int KIND = MULTI_FUSED;
     SWG_MULTI_CASE(16, 8)
+    SWG_MULTI_CASE(16, 32)
     SWG_MULTI_CASE(32, 8)
     SWG_MULTI_CASE(32, 12)
     SWG_MULTI_CASE(32, 16)

@@ -63,6 +63,7 @@ int launch_split_plan(const Plan &pl, const BatchArgs &a, int num_sms, cudaStrea
     SWG_CASE(2, 16)
     SWG_CASE(2, 32)
     SWG_CASE(16, 8)
+    SWG_CASE(16, 32)
     SWG_CASE(32, 8)
     SWG_CASE(32, 12)
     SWG_CASE(32, 16)
@@ -96,6 +97,7 @@ int launch_split_plan_pieces(const Plan &pl, const BatchArgs &a, int num_sms, cu
     SWG_CASE(2, 16)
     SWG_CASE(2, 32)
     SWG_CASE(16, 8)
+    SWG_CASE(16, 32)
     SWG_CASE(32, 8)
     SWG_CASE(32, 12)
     SWG_CASE(32, 16)

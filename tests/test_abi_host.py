@@ -91,7 +91,7 @@ def test_plan_query_covers_the_query_host_only(swlib):
                 assert m / (p["chunks"] * QC) > 0.5
     picks = {m: swlib.sw_plan_query(m) for m in (128, 512, 2048, 5000)}
     assert picks[128] == dict(lanes=16, seg_len=8, chunks=1, lane_type=4)
-    assert picks[512] == dict(lanes=64, seg_len=8, chunks=1, lane_type=4)
+    assert picks[512] == dict(lanes=16, seg_len=32, chunks=1, lane_type=4)
     assert picks[2048] == dict(lanes=64, seg_len=32, chunks=1, lane_type=4)
     assert picks[5000] == dict(lanes=32, seg_len=40, chunks=4, lane_type=4)
     # lengths between the benchmark's: the layout whose chunk the query fills

@@ -21,8 +21,8 @@ ALL_PLANS = {
         (8, 32), (16, 32), (32, 32)],
     2: [(8, 8), (8, 16), (16, 8), (16, 16), (32, 8), (32, 12), (32, 16), (16, 32), (32, 24), (32, 32)],
     3: [(8, 16), (16, 16), (32, 16)],
-    4: [(2, 16), (2, 32), (16, 8), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (32, 40), (64, 8),
-        (64, 16), (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)],
+    4: [(2, 16), (2, 32), (16, 8), (16, 32), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (32, 40),
+        (64, 8), (64, 16), (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)],
 }
 
 
@@ -248,8 +248,8 @@ def test_batched_launch_every_layout_exact(sw):
     M = synth.protein_matrix(rng)
     lens = np.concatenate([[0, 1, 2, 5], synth.lengths_lognormal(rng, 150, 300, 0.76, 20, 3000)])
     seqs = [synth.residues(rng, int(x), 20) for x in lens]
-    layouts = [(16, 8), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (32, 40), (64, 8), (64, 16),
-               (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)]
+    layouts = [(16, 8), (16, 32), (32, 8), (32, 12), (32, 16), (32, 20), (32, 24), (32, 32), (32, 40), (64, 8),
+               (64, 16), (64, 20), (64, 24), (64, 28), (64, 32), (64, 40)]
     queries, lays = [], []
     for k, lay in enumerate(layouts):
         for m in (max(1, lay[0] * lay[1] - 3), 2 * lay[0] * lay[1] + 5):  # one chunk, three chunks

@@ -207,8 +207,8 @@ def test_both_corrected_passes(sw, kind):
                                                   % (o, e, mm, len(q)))
 
 
-AC_LAYOUTS = [(16, 8), (32, 8), (32, 16), (32, 24), (32, 32), (32, 40), (64, 8), (64, 16), (64, 24), (64, 28),
-              (64, 32), (64, 40)]
+AC_LAYOUTS = [(16, 8), (16, 32), (32, 8), (32, 16), (32, 24), (32, 32), (32, 40), (64, 8), (64, 16), (64, 24),
+              (64, 28), (64, 32), (64, 40)]
 
 
 @pytest.mark.parametrize("layout", AC_LAYOUTS)
