@@ -977,10 +977,11 @@ def ragged_summary(args, n_queries):
     db_d = torch.from_numpy(db).cuda()
     off_d = torch.from_numpy(off).cuda()
     h = sw.Database(db_d, off_d)
-    # autotune against the database itself (one query per length bin), over
-    # the split layouts the batched launch runs
+    # autotune against the database itself over the split layouts the
+    # batched launch runs, each timed as one batched launch of 4 queries of
+    # the bin's length (the batch's own setting: no per-query launch tail)
     table = autotune.tune(h, M, 11, 1, lengths=[48, 100, 200, 400, 800, 1600, 3200], reps=1,
-                          lanes=(sw.SW_LANE_I16X2Q,))
+                          lanes=(sw.SW_LANE_I16X2Q,), batched=4)
     out = torch.empty((len(queries), h.n), dtype=torch.int32, device="cuda")
     ba = BatchAligner(h, M, 11, 1, table=table, streams=args.streams).prepare(queries, out)
     st = ba.stream

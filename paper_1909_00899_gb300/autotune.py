@@ -137,11 +137,39 @@ def _time_layout(db, query, M, o, e, lane, L, S, out, reps, stream):
         prof.free()
 
 
+def _time_layout_multi(db, queries, M, o, e, L, S, out, reps, stream):
+    """ms per query of one batched launch (sw_align_multi) over `queries`,
+    all of one length on one split layout: the way a ragged batch runs
+    them, where the launch's tail is one query's, not every query's."""
+    import torch
+    profs = [sw.Profile(q, M, sw.SW_LANE_I16X2Q, stream=stream, lanes=L, seg_len=S) for q in queries]
+    batch = None
+    try:
+        batch = sw.Multi(profs, db, stream=stream)
+        sw.sw_align_multi(batch, o, e, out, stream=stream)  # warm-up
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            sw.sw_align_multi(batch, o, e, out, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps / len(queries)
+    finally:
+        if batch is not None:
+            batch.free()
+        for p in profs:
+            p.free()
+
+
 def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I16X2Q, sw.SW_LANE_I32), reps=2, seed=0,
-         device_name=None, verbose=False):
+         device_name=None, verbose=False, batched=0):
     """Times every admissible layout for one query per length bin against
     the resident database `db` and returns each layout's rate per processed
-    cell, per bin."""
+    cell, per bin.  batched = k > 0 times the split layouts of the batched
+    launch (16 or more virtual lanes) as one sw_align_multi over k queries
+    of the length instead, the rate a ragged batch sees (no per-query
+    launch tail); use that table with BatchAligner's batched mode."""
     import torch
     rng = np.random.default_rng(seed)
     A = M.shape[0]
@@ -150,14 +178,20 @@ def tune(db, M, o, e, lengths=None, lanes=(sw.SW_LANE_I16X2, sw.SW_LANE_I16X2Q, 
     out = torch.empty(max(db.n, 1), dtype=torch.int32, device="cuda")
     lengths = lengths or [min(b, 6000) for b in BINS]
     best = {}
+    if batched:
+        out_k = torch.empty((batched, max(db.n, 1)), dtype=torch.int32, device="cuda")
     for m in lengths:
         q = rng.integers(0, A, m).astype(np.uint8)
+        qs = [q] + [rng.integers(0, A, m).astype(np.uint8) for _ in range(max(0, batched - 1))]
         cands = []
         for lane in lanes:
             for (L, S) in CANDIDATES[lane]:
                 if not admissible(m, L, S):
                     continue
-                ms = _time_layout(db, q, M, o, e, lane, L, S, out, reps, stream)
+                if batched and lane == sw.SW_LANE_I16X2Q and L >= 16:
+                    ms = _time_layout_multi(db, qs, M, o, e, L, S, out_k, reps, stream)
+                else:
+                    ms = _time_layout(db, q, M, o, e, lane, L, S, out, reps, stream)
                 C = chunks_of(m, L, S)
                 # per processed cell, with the extra chunk launches of this
                 # length taken out again (expected_gcups charges them per m)

@@ -357,6 +357,32 @@ def test_autotuner_table_is_exact(sw, small_db):
     ba.free()
 
 
+def test_autotuner_batched_timing_is_exact(sw, small_db):
+    """The tuner's batched timing (one sw_align_multi over k queries per
+    layout) gives a table whose plans the batched launch runs exactly."""
+    from paper_1909_00899_gb300 import autotune
+    from paper_1909_00899_gb300.batch import BatchAligner
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    table = autotune.tune(h, M, 11, 1, lengths=[150, 1500], reps=1, lanes=(sw.SW_LANE_I16X2Q,), batched=2)
+    for m in (150, 1500):
+        assert table.plan(m) is not None and table.plan(m)[0] == sw.SW_LANE_I16X2Q
+        assert all(c[3] > 0 for c in table.entries[autotune.bin_of(m)])
+    rng = np.random.default_rng(2015)
+    queries = [synth.residues(rng, m, 20) for m in (120, 150, 1400, 1500)]
+    out = torch.empty((len(queries), h.n), dtype=torch.int32, device="cuda")
+    ba = BatchAligner(h, M, 11, 1, table=table).prepare(queries, out)
+    assert ba.multi is not None
+    ba.run()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for i, q in enumerate(queries):
+        np.testing.assert_array_equal(got[i], oracle.gotoh_batch(q, db, off, M, 11, 1))
+    ba.free()
+    h.free()
+
+
 def test_serving_admits_by_available_device_memory(sw, small_db, monkeypatch):
     """Admission also checks the memory the device has now: with the query
     reporting too little, requests wait while others of the server run and
