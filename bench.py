@@ -545,15 +545,23 @@ def main():
         # the other workloads, each with its own clock record and an oracle
         # spot check: reads vs windows with the lazy-F worst case, the
         # ragged batch, serving
+        # (a failure in one is recorded under its key; the scale step's
+        # numbers above stand and the line is still printed)
         del outs, db_d, off_d, flush
         torch.cuda.empty_cache()
-        pl = pairs_summary(args, cpu=False)
-        line["gap_adversary"] = pl.pop("gap_adversary")
-        line["pairs"] = pl
-        torch.cuda.empty_cache()
-        line["ragged"] = ragged_summary(args, args.extras_queries)
-        torch.cuda.empty_cache()
-        line["serving"] = serving_summary(args, args.extras_requests)
+        try:
+            pl = pairs_summary(args, cpu=False)
+            line["gap_adversary"] = pl.pop("gap_adversary")
+            line["pairs"] = pl
+        except Exception as ex:  # noqa: BLE001 -- reported in the line
+            line["pairs"] = line["gap_adversary"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+        for key, fn in (("ragged", lambda: ragged_summary(args, args.extras_queries)),
+                        ("serving", lambda: serving_summary(args, args.extras_requests))):
+            torch.cuda.empty_cache()
+            try:
+                line[key] = fn()
+            except Exception as ex:  # noqa: BLE001 -- reported in the line
+                line[key] = {"error": "%s: %s" % (type(ex).__name__, ex)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
