@@ -280,7 +280,10 @@ def test_batched_launch_general_pass_and_dna(sw):
     queries = queries[:6] + [synth.residues(rng, n, 4) for n in (70, 700, 2100, 4000)]
     for o, e, mm in ((6, 1, -4), (3, 1, -5), (5, 5, -2)):
         M = synth.dna_matrix(match=2, mismatch=mm)
-        _multi_case(sw, M, o, e, refs, queries, [None] * len(queries))
+        got, _, _ = _multi_case(sw, M, o, e, refs, queries, [None] * len(queries))
+        if mm < -o:  # the general pass in the fused-chunk tiles as well
+            got2, _, _ = _multi_case(sw, M, o, e, refs, queries, [None] * len(queries), items_per_group=2)
+            np.testing.assert_array_equal(got2, got)
 
 
 def test_batched_launch_wait_bound_sets_status(sw, small_db):
