@@ -271,14 +271,15 @@ def test_batched_launch_every_layout_exact(sw):
 def test_batched_launch_general_pass_and_dna(sw):
     """The batched launch with mismatch scores below -o (the general
     corrected pass) and with DNA scoring (most h below zero: the always-
-    corrected pass's floor on the diagonal), query-side insertions across
-    many lanes and chunks."""
+    corrected pass's floor on the diagonal), gap extension 0 (carries that
+    never decay) and e = o, query-side insertions across many lanes and
+    chunks."""
     from helpers import gap_adversary
     rng = np.random.default_rng(2011)
     queries, refs = gap_adversary(rng, 4, 20, ylo=60, yhi=500)
     refs += [synth.residues(rng, int(n), 4) for n in (1, 7, 900, 2500)]
     queries = queries[:6] + [synth.residues(rng, n, 4) for n in (70, 700, 2100, 4000)]
-    for o, e, mm in ((6, 1, -4), (3, 1, -5), (5, 5, -2)):
+    for o, e, mm in ((6, 1, -4), (3, 1, -5), (5, 5, -2), (4, 0, -2), (2, 0, -5)):
         M = synth.dna_matrix(match=2, mismatch=mm)
         got, _, _ = _multi_case(sw, M, o, e, refs, queries, [None] * len(queries))
         if mm < -o:  # the general pass in the fused-chunk tiles as well
