@@ -318,6 +318,42 @@ def test_batched_launch_wait_bound_sets_status(sw, small_db):
     h.free()
 
 
+def test_batched_launch_empty_batch_and_empty_database(sw, small_db):
+    """No queries, an empty database, and a batch of only empty queries:
+    the calls succeed, launch nothing that writes outside the score rows,
+    and empty queries score 0."""
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    none = sw.Multi([], h)
+    out = torch.full((1, h.n), -3, dtype=torch.int32, device="cuda")
+    sw.sw_align_multi(none, 11, 1, out)
+    torch.cuda.synchronize()
+    assert (out == -3).all()
+    assert sw.sw_multi_status(none) == 0
+    none.free()
+    empties = [sw.Profile(np.zeros(0, np.uint8), M) for _ in range(2)]
+    batch = sw.Multi(empties, h)
+    out2 = torch.full((2, h.n + 3), -3, dtype=torch.int32, device="cuda")
+    sw.sw_align_multi(batch, 11, 1, out2)
+    torch.cuda.synchronize()
+    got = out2.cpu().numpy()
+    assert (got[:, :h.n] == 0).all() and (got[:, h.n:] == -3).all()
+    batch.free()
+    empty_db = sw.Database(torch.zeros(0, dtype=torch.uint8, device="cuda"),
+                           torch.zeros(1, dtype=torch.int64, device="cuda"))
+    q = sw.Profile(synth.residues(np.random.default_rng(2016), 3000, 20), M)
+    b2 = sw.Multi([q], empty_db)
+    sw.sw_align_multi(b2, 11, 1, torch.empty((1, 1), dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    assert sw.sw_multi_status(b2) == 0
+    b2.free()
+    for p in empties + [q]:
+        p.free()
+    empty_db.free()
+    h.free()
+
+
 def test_batched_launch_rejects_what_it_cannot_run(sw, small_db):
     M, db, off = small_db["M"], small_db["db"], small_db["off"]
     db_d, off_d = db_to_dev(db, off)
