@@ -354,6 +354,29 @@ def test_batched_launch_empty_batch_and_empty_database(sw, small_db):
     h.free()
 
 
+def test_batch_aligner_falls_back_to_per_query_calls(sw, small_db):
+    """Gap costs beyond the packed lanes of the batched launch (o > 127) and
+    profiles on other lane types: the aligner captures per-query calls
+    instead, with the same exact scores."""
+    from paper_1909_00899_gb300.batch import BatchAligner
+    M, db, off = small_db["M"], small_db["db"], small_db["off"]
+    db_d, off_d = db_to_dev(db, off)
+    h = sw.Database(db_d, off_d)
+    rng = np.random.default_rng(2017)
+    queries = [synth.residues(rng, m, 20) for m in (40, 300, 1500)]
+    for o, e, lane in ((150, 3, sw.SW_LANE_AUTO), (11, 1, sw.SW_LANE_I32)):
+        out = torch.full((len(queries), h.n), -1, dtype=torch.int32, device="cuda")
+        ba = BatchAligner(h, M, o, e, lane=lane).prepare(queries, out)
+        assert ba.multi is None and ba.mode == "per_query"
+        ba.run()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for i, q in enumerate(queries):
+            np.testing.assert_array_equal(got[i], oracle.gotoh_batch(q, db, off, M, o, e), err_msg="o=%d" % o)
+        ba.free()
+    h.free()
+
+
 def test_batched_launch_rejects_what_it_cannot_run(sw, small_db):
     M, db, off = small_db["M"], small_db["db"], small_db["off"]
     db_d, off_d = db_to_dev(db, off)
